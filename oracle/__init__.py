@@ -1,0 +1,186 @@
+"""CPU oracle of the thermal D2Q37 lattice Boltzmann step (FP64).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg may import this package.  The product library
+under ``paper_1703_00185_gb300/`` never imports, links or calls it.
+
+Parts:
+  * ``quadrature``  velocity set and weights (50-digit Newton solve);
+  * ``d2q37_oracle.c``  the plain FP64 step (pbc, pull propagate, wall bc,
+    BGK collide with the shifted 4th-order Hermite equilibrium), built with
+    gcc ``-O2 -ffp-contract=off`` and driven through ``ctypes`` here;
+  * ``naive``  a second, independent numpy formulation used to brute-force
+    check the C oracle on tiny lattices.
+
+All arrays crossing this interface are float64 numpy arrays.  Populations
+are ``[37, Lx, Ly]`` in this oracle's own velocity order (``velocity_set()``);
+fields are ``rho[Lx, Ly]``, ``u[2, Lx, Ly]``, ``T[Lx, Ly]``.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+from . import quadrature
+
+Q = 37
+PHASE_PROPAGATE, PHASE_BC, PHASE_COLLIDE = 1, 2, 4
+PHASE_ALL = 7
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "d2q37_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle_d2q37.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile the C oracle with gcc (FP contraction off, OpenMP on)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-shared", "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.orc_setup.argtypes = [ctypes.c_double, dp]
+    lib.orc_setup.restype = ctypes.c_int
+    lib.orc_velocity_set.argtypes = [ip, ip]
+    lib.orc_weights.argtypes = [dp]
+    lib.orc_threads.restype = ctypes.c_int
+    lib.orc_equilibrium.argtypes = [ctypes.c_double] * 4 + [dp]
+    lib.orc_site_moments.argtypes = [dp, dp, dp, dp, dp]
+    lib.orc_collide_site.argtypes = [dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+    lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + [ctypes.c_int]
+    lib.orc_create.restype = ctypes.c_void_p
+    lib.orc_destroy.argtypes = [ctypes.c_void_p]
+    lib.orc_set_populations.argtypes = [ctypes.c_void_p, dp]
+    lib.orc_get_populations.argtypes = [ctypes.c_void_p, dp]
+    lib.orc_run.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    lib.orc_run.restype = ctypes.c_int
+    lib.orc_fields.argtypes = [ctypes.c_void_p, dp, dp, dp]
+    lib.orc_splitmix64.argtypes = [ctypes.c_uint64]
+    lib.orc_splitmix64.restype = ctypes.c_uint64
+    lib.orc_rt_temperature.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_double,
+                                       ctypes.c_double, dp]
+    lib.orc_init_rayleigh_taylor.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    s, w = quadrature.weights_fp64()
+    wa = (ctypes.c_double * 8)(*w)
+    if lib.orc_setup(s, wa) != Q:
+        raise RuntimeError("oracle set-up failed")
+    _lib = lib
+    return lib
+
+
+def _p(a):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def velocity_set():
+    """(cx, cy) int arrays of the 37 hops in this oracle's order."""
+    lib = _load()
+    cx = (ctypes.c_int * Q)()
+    cy = (ctypes.c_int * Q)()
+    lib.orc_velocity_set(cx, cy)
+    return np.array(cx[:]), np.array(cy[:])
+
+
+def scale_and_weights():
+    """(s, w[37]) as used by the oracle."""
+    lib = _load()
+    w = np.zeros(Q)
+    lib.orc_weights(_p(w))
+    return quadrature.weights_fp64()[0], w
+
+
+def threads():
+    return _load().orc_threads()
+
+
+def equilibrium(rho, ux, uy, T):
+    """f^eq_l(rho, u, T) for the 37 velocities (4th-order Hermite)."""
+    out = np.zeros(Q)
+    _load().orc_equilibrium(rho, ux, uy, T, _p(out))
+    return out
+
+
+def site_moments(f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    r = [ctypes.c_double() for _ in range(4)]
+    _load().orc_site_moments(_p(f), *[ctypes.byref(x) for x in r])
+    return tuple(x.value for x in r)
+
+
+def collide_site(f, tau, gx, gy):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(Q)
+    _load().orc_collide_site(_p(f), tau, gx, gy, _p(out))
+    return out
+
+
+def splitmix64(v):
+    return _load().orc_splitmix64(v)
+
+
+def rt_temperature(Lx, Ly, seed, T_top=0.5, T_bot=1.5):
+    T = np.zeros((Lx, Ly))
+    _load().orc_rt_temperature(Lx, Ly, seed, T_top, T_bot, _p(T))
+    return T
+
+
+class Lattice:
+    """An Lx x Ly lattice (x periodic; walls at y = 0 and y = Ly - 1 unless
+    ``periodic_y``), gravity g = (0, -g0)."""
+
+    def __init__(self, Lx, Ly, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5, periodic_y=False):
+        self._lib = _load()
+        self.Lx, self.Ly = Lx, Ly
+        self.tau, self.g0, self.T_top, self.T_bot = tau, g0, T_top, T_bot
+        self.periodic_y = bool(periodic_y)
+        self._h = self._lib.orc_create(Lx, Ly, tau, g0, T_top, T_bot, int(periodic_y))
+        if not self._h:
+            raise ValueError("invalid lattice parameters")
+
+    def close(self):
+        if self._h:
+            self._lib.orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (Q, self.Lx, self.Ly)
+        self._lib.orc_set_populations(self._h, _p(f))
+
+    def populations(self):
+        f = np.zeros((Q, self.Lx, self.Ly))
+        self._lib.orc_get_populations(self._h, _p(f))
+        return f
+
+    def init_rayleigh_taylor(self, seed):
+        self._lib.orc_init_rayleigh_taylor(self._h, seed)
+
+    def run(self, nsteps=1, phases=PHASE_ALL):
+        if self._lib.orc_run(self._h, nsteps, phases) != 0:
+            raise ValueError("bad phase mask %d" % phases)
+
+    def fields(self):
+        n = self.Lx * self.Ly
+        rho, u, T = np.zeros(n), np.zeros(2 * n), np.zeros(n)
+        self._lib.orc_fields(self._h, _p(rho), _p(u), _p(T))
+        return rho.reshape(self.Lx, self.Ly), u.reshape(2, self.Lx, self.Ly), T.reshape(self.Lx, self.Ly)
