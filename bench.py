@@ -1,0 +1,286 @@
+#!/usr/bin/env python3
+"""Throughput of the thermal D2Q37 time step on GB300.
+
+One step = pbc + fused propagate/bc/collide over the whole lattice (or the
+four separate kernels with --kernel separate).  Default workload: one
+2048 x 8192 Rayleigh-Taylor lattice in FP64, populations resident in HBM
+(two copies, 2 x 5.0 GB, far larger than the 129 MB L2, so no flush is
+needed between steps).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank advances its own lattice (replicas; weak scaling,
+no collective on the data path).  ``--impl reference`` times the CPU oracle
+on the host cores instead (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS per step"
+UNIT = "MLUPS"
+BYTES_PER_SITE = 592          # 37 FP64 populations read + 37 written per site update
+# FP64 flops the fused kernel executes per site: DADD + DMUL + 2 DFMA from the
+# ncu instruction counters of the fused kernel (89.15 + 107.06 + 2 x 209.00)
+FP64_FLOPS_PER_SITE = 614.2
+# FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--kernel", choices=["fused", "separate"], default="fused")
+    ap.add_argument("--Lx", type=int, default=2048)
+    ap.add_argument("--Ly", type=int, default=8192)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def workload_name(a):
+    return "rayleigh_taylor_fp64_%dx%d" % (a.Lx, a.Ly)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_mlups(Lx, Ly, seconds, max_steps=None):
+    """Time full oracle steps on an Lx x Ly Rayleigh-Taylor lattice."""
+    import oracle
+    lat = oracle.Lattice(Lx, Ly, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5)
+    lat.init_rayleigh_taylor(1)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        lat.run(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps and steps >= max_steps):
+            break
+    lat.close()
+    return Lx * Ly * steps / el / 1e6, steps, el, oracle.threads()
+
+
+def cpu_baseline(a):
+    Ly = max(6, a.Ly // 8)
+    v, steps, el, cores = oracle_mlups(a.Lx, Ly, a.cpu_seconds)
+    return {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d full oracle steps (pbc+propagate+bc+collide, FP64) of a %dx%d Rayleigh-Taylor lattice "
+                      "(1/8 of the %dx%d workload's rows), %.1f s" % (steps, a.Lx, Ly, a.Lx, a.Ly, el)}
+
+
+def run_reference(a):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    Ly = 64  # a bounded sample of the workload per step: full width, 64 rows
+    lat = oracle.Lattice(a.Lx, Ly, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5)
+    lat.init_rayleigh_taylor(1)
+    lat.run(a.warmup)
+    t0 = time.perf_counter()
+    lat.run(a.steps)
+    el = time.perf_counter() - t0
+    v = a.Lx * Ly * a.steps / el / 1e6
+    cores = oracle.threads()
+    sample = "each step: one full oracle step (FP64, pbc+propagate+bc+collide) of a %dx%d strip of the %dx%d " \
+             "Rayleigh-Taylor workload" % (a.Lx, Ly, a.Lx, a.Ly)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(el / a.steps * 1e3, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "Lx": a.Lx, "Ly": a.Ly, "sample_Ly": Ly},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- GPU arm
+
+def run_ours(a):
+    rank, local_rank, world = dist_env()
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(a)  # before any CUDA work in this process
+    import torch
+    import paper_1703_00185_gb300 as lbm
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    sites = a.Lx * a.Ly
+    lat = lbm.Lattice(a.Lx, a.Ly, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5, kernel=a.kernel, device=dev)
+    lat.init_rayleigh_taylor(1 + rank)
+    for _ in range(a.warmup):
+        lat.step(1)
+    lat.synchronize()
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    sampler = ClockSampler("GPU-" + str(uuid) if uuid is not None else None)
+    lat.set_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)  # let nvidia-smi take its first samples
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = lat.launch_count
+    e0.record(lat.stream)
+    for _ in range(a.steps):
+        lat.step(1)
+    e1.record(lat.stream)
+    e1.synchronize()
+    torch.cuda.synchronize(dev)
+    launches = lat.launch_count - n0
+    ms = e0.elapsed_time(e1)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    kt = lat.kernel_times()
+    lat.set_timing(False)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / a.steps
+    value = sites * world * a.steps / (ms * 1e-3) / 1e6
+
+    # dominant kernel of the timed region, its average launch from events on the launching stream
+    kind = max(kt, key=lambda k: kt[k][0])
+    kms, kn = kt[kind]
+    avg_s = kms / kn * 1e-3
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    site_launch = sites
+    roofline = {"bound": "alu", "kernel": kind, "achieved": None, "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
+    if kind in ("fused", "collide"):
+        achieved = FP64_FLOPS_PER_SITE * site_launch / avg_s / 1e12
+        roofline.update(achieved=round(achieved, 4), frac=round(achieved / FP64_PEAK_TFLOPS, 4))
+    hbm_bytes = (BYTES_PER_SITE if kind in ("fused", "propagate", "collide") else 0) * site_launch
+    roofline["hbm"] = {"algorithmic_bytes_per_launch": hbm_bytes,
+                       "achieved_gbs": round(hbm_bytes / avg_s / 1e9, 1),
+                       "peak_gbs": hbm_peak, "frac": round(hbm_bytes / avg_s / 1e9 / hbm_peak, 4) if hbm_peak else None,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roofline["avg_launch_ms"] = round(avg_s * 1e3, 4)
+
+    # end to end through the C ABI with pinned host buffers: upload state, one step, read fields
+    e2e = None
+    if a.e2e_steps > 0:
+        f_host = torch.empty((37, a.Lx, a.Ly), dtype=torch.float64, pin_memory=True)
+        lat.populations(out=f_host.numpy())
+        rho = torch.empty((a.Lx, a.Ly), dtype=torch.float64, pin_memory=True)
+        u = torch.empty((2, a.Lx, a.Ly), dtype=torch.float64, pin_memory=True)
+        T = torch.empty((a.Lx, a.Ly), dtype=torch.float64, pin_memory=True)
+        lat.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            lat.set_populations(f_host)
+            lat.step(1)
+            lat.fields(out=(rho, u, T))
+        el = time.perf_counter() - t0
+        e2e = {"value": round(sites * world * a.e2e_steps / el / 1e6, 3), "unit": UNIT,
+               "h2d_bytes_per_step": f_host.numel() * 8,
+               "d2h_bytes_per_step": (rho.numel() + u.numel() + T.numel()) * 8,
+               "steps": a.e2e_steps}
+    lat.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload_name(a), "Lx": a.Lx, "Ly": a.Ly, "kernel": a.kernel,
+                           "tau": 0.8, "g0": 1e-4, "T_top": 0.5, "T_bot": 1.5, "seed": "1 + rank",
+                           "l2": "no flush: inputs exceed L2 (2 x %.2f GB population copies vs 129 MB)" %
+                                 (37 * (a.Lx + 6) * (a.Ly + 32) * 8 / 1e9),
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "kernel_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]}, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * d2q37.h - C ABI of the GB300 (sm_103a) thermal D2Q37 lattice Boltzmann step.
+ *
+ * One time step of the method of Calore et al., "Massively parallel lattice
+ * Boltzmann codes on large GPU clusters": pbc (periodic x halos) -> propagate
+ * (pull form, Eq. master2) -> bc (top/bottom walls) -> collide (BGK relaxation
+ * to the shifted equilibrium of Eq. MASTERSHIFT3, Eq. discrete), or a fused
+ * propagate+collide pass (Sec. "Performance Analysis", last paragraph, and the
+ * fused kernels of Sec. "2D Splitting").
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: LBM_OK (0) on success, a negative LBM_E* code on failure;
+ *    lbm_strerror() gives its text.  No entry point aborts the process.
+ *  - Lattice: Lx x Ly physical sites, x periodic, y bounded by a bottom wall
+ *    (y = 0 side, temperature T_bot) and a top wall (y = Ly - 1 side, T_top)
+ *    unless periodic_y is set.  Gravity g = (0, -g0).  Lengths are in lattice
+ *    sites, time in steps, velocities and temperatures in the thermal units
+ *    of the quadrature (reference temperature 1).
+ *  - Host field arrays are caller-owned FP64, site (x, y) at index x*Ly + y.
+ *    Population arrays are [37][Lx][Ly], population order as returned by
+ *    lbm_velocity_set().
+ *  - All work is enqueued on the handle's CUDA stream and is asynchronous
+ *    unless an entry point says it synchronises.  A handle is not thread-safe;
+ *    separate handles may be driven from separate threads and streams.
+ *  - The library never frees memory it did not allocate.
+ */
+#ifndef D2Q37_H
+#define D2Q37_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_Q 37
+
+#define LBM_OK 0
+#define LBM_EINVAL (-1)   /* bad argument: NULL, Lx < 3, Ly < 6, tau <= 0.5, bad phase mask */
+#define LBM_ENOMEM (-2)   /* device allocation failed, or caller buffer too small */
+#define LBM_ECUDA (-3)    /* a CUDA call or kernel launch failed */
+#define LBM_ETIMEOUT (-4) /* reserved for bounded device waits */
+#define LBM_ESTATE (-5)   /* call out of order, e.g. a step before any initial state */
+
+/* Phase bits for lbm_run_phases(). */
+#define LBM_PHASE_PROPAGATE 1 /* pbc + pull propagate (Sec. "Code Organization") */
+#define LBM_PHASE_BC 2        /* wall bc; only together with LBM_PHASE_PROPAGATE */
+#define LBM_PHASE_COLLIDE 4   /* BGK collide (Eq. discrete) */
+#define LBM_PHASE_ALL 7
+
+/* Kernel schedules for lbm_params.kernel. */
+#define LBM_KERNEL_SEPARATE 0 /* pbc, propagate, bc, collide as separate kernels */
+#define LBM_KERNEL_FUSED 1    /* pbc, then one fused propagate+bc+collide kernel */
+
+typedef struct lbm_t lbm_t;
+
+typedef struct {
+  double tau;     /* BGK relaxation time in steps, > 0.5 (paper: symbol tau, value not given) */
+  double g0;      /* gravity magnitude; g = (0, -g0) */
+  double T_top;   /* top wall temperature */
+  double T_bot;   /* bottom wall temperature */
+  int precision;  /* 0 = FP64 populations (the only value accepted by this version) */
+  int kernel;     /* LBM_KERNEL_SEPARATE or LBM_KERNEL_FUSED */
+  int periodic_y; /* 1: no walls, y periodic too (used by tests of pure propagation) */
+} lbm_params;
+
+/* Defaults: tau 0.8, g0 1e-4, T_top 0.5, T_bot 1.5, FP64, fused, walls. */
+void lbm_default_params(lbm_params* p);
+
+/* The 37 integer hops c_l = (cx[l], cy[l]) in this library's population
+ * order (Sec. "Lattice Boltzmann methods": labels are arbitrary).  cx, cy are
+ * caller arrays of 37 ints.  Host only; never fails for non-NULL pointers. */
+int lbm_velocity_set(int* cx, int* cy);
+
+/* Thermal scale s (xi_l = s c_l) and the 37 weights w_l in population order,
+ * solved by this library at first use.  Host only. */
+int lbm_quadrature(double* s, double* w);
+
+/* Device bytes needed for an Lx x Ly lattice: two FP64 population copies
+ * of 37 x (Lx+6) x NY sites (NY = Ly + 32 rounded up to a multiple of 16)
+ * plus field scratch.  0 for invalid sizes. */
+size_t lbm_required_bytes(int Lx, int Ly, const lbm_params* p);
+
+/* Create a lattice on the current CUDA device; allocates its own device
+ * memory (cudaMalloc) and its own stream.  *out is set only on success. */
+int lbm_create(int Lx, int Ly, const lbm_params* p, lbm_t** out);
+
+/* As lbm_create, but the device memory is the caller's: dev_buf (256-byte
+ * aligned, at least lbm_required_bytes) stays owned by the caller and must
+ * outlive the handle; cuda_stream is a cudaStream_t (NULL: legacy default
+ * stream) on which all work of this handle is enqueued. */
+int lbm_create_ext(int Lx, int Ly, const lbm_params* p, void* dev_buf, size_t bytes, void* cuda_stream,
+                   lbm_t** out);
+
+/* Rayleigh-Taylor initial state (the workload of Sec. "Overview of Physics
+ * Results"): cold T_top fluid over hot T_bot fluid, interface
+ * y_i(x) = Ly/2 + (Ly/64) sin(2 pi (x + 1/2) / Lx), T scaled by
+ * 1 + 1e-3 (2U - 1), U = (splitmix64(seed + x Ly + y) >> 11) 2^-53;
+ * rho = 1/T, u = 0, populations at equilibrium.  The temperature field is
+ * built on the host (host-side scratch of 8 Lx Ly bytes) and uploaded; this
+ * call synchronises the handle's stream. */
+int lbm_init_rayleigh_taylor(lbm_t* h, uint64_t seed);
+
+/* Upload / download all physical populations, host [37][Lx][Ly] FP64 in this
+ * library's order.  Pinned host memory makes the copies asynchronous; the
+ * download synchronises the stream before returning. */
+int lbm_set_populations(lbm_t* h, const double* f);
+int lbm_get_populations(lbm_t* h, double* f);
+
+/* n full time steps (pbc -> propagate -> bc -> collide, Sec. "Code
+ * Organization"), asynchronous on the handle's stream. */
+int lbm_step(lbm_t* h, int n);
+
+/* n repetitions of the selected phases (LBM_PHASE_* bits) with the separate
+ * kernels, for phase-by-phase checking.  BC requires PROPAGATE. */
+int lbm_run_phases(lbm_t* h, int n, int phases);
+
+/* Macroscopic fields of the current populations (Sec. "Lattice Boltzmann
+ * methods": rho = sum f, rho u = sum xi f, D rho T = sum |xi - u|^2 f).
+ * Host arrays rho[Lx Ly], u[2 Lx Ly] (ux plane then uy plane), T[Lx Ly];
+ * synchronises the stream. */
+int lbm_fields(lbm_t* h, double* rho, double* u, double* T);
+
+/* Same fields into caller device arrays, asynchronous on the stream. */
+int lbm_fields_device(lbm_t* h, double* rho, double* u, double* T);
+
+/* Wait for all work enqueued on the handle's stream; reports any
+ * asynchronous CUDA error as LBM_ECUDA. */
+int lbm_synchronize(lbm_t* h);
+
+/* Number of CUDA kernel launches this handle has enqueued so far. */
+int64_t lbm_launch_count(const lbm_t* h);
+
+/* Kernel kinds reported by lbm_kernel_times(). */
+#define LBM_KIND_WRAP 0
+#define LBM_KIND_PROPAGATE 1
+#define LBM_KIND_BC 2
+#define LBM_KIND_COLLIDE 3
+#define LBM_KIND_FUSED 4
+#define LBM_KIND_FIELDS 5
+#define LBM_KIND_INIT 6
+#define LBM_KIND_COUNT 7
+
+/* Per-kernel timing (not in the paper; measurement support).  enable != 0
+ * records a CUDA event pair on the handle's stream around every later kernel
+ * launch of this handle and clears the totals; 0 stops recording. */
+int lbm_set_timing(lbm_t* h, int enable);
+
+/* Totals since timing was enabled: ms[LBM_KIND_COUNT] of device time per
+ * kernel kind and launches[LBM_KIND_COUNT] (either may be NULL).
+ * Synchronises the stream. */
+int lbm_kernel_times(lbm_t* h, double* ms, int64_t* launches);
+
+/* Release the handle and the device memory it allocated.  NULL-safe. */
+void lbm_destroy(lbm_t* h);
+
+const char* lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* D2Q37_H */

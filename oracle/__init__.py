@@ -76,6 +76,7 @@ def _load():
     lib.orc_rt_temperature.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_double,
                                        ctypes.c_double, dp]
     lib.orc_init_rayleigh_taylor.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    lib.orc_set_equilibrium.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
     s, w = quadrature.weights_fp64()
     wa = (ctypes.c_double * 8)(*w)
     if lib.orc_setup(s, wa) != Q:
@@ -171,6 +172,11 @@ class Lattice:
         f = np.zeros((Q, self.Lx, self.Ly))
         self._lib.orc_get_populations(self._h, _p(f))
         return f
+
+    def set_equilibrium(self, rho, ux, uy, T):
+        """Populations at equilibrium with the given [Lx, Ly] fields."""
+        a = [np.ascontiguousarray(np.broadcast_to(v, (self.Lx, self.Ly)), dtype=np.float64) for v in (rho, ux, uy, T)]
+        self._lib.orc_set_equilibrium(self._h, *[_p(v) for v in a])
 
     def init_rayleigh_taylor(self, seed):
         self._lib.orc_init_rayleigh_taylor(self._h, seed)

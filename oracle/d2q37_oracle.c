@@ -361,6 +361,20 @@ void orc_fields(const orc_lattice* a, double* rho, double* u, double* T) {
   }
 }
 
+/* Populations at equilibrium with given fields, each [x * Ly + y]. */
+void orc_set_equilibrium(orc_lattice* a, const double* rho, const double* ux, const double* uy, const double* T) {
+  double* d = a->buf[a->cur];
+#pragma omp parallel for schedule(static)
+  for (int x = 0; x < a->Lx; ++x) {
+    double feq[Q];
+    for (int y = 0; y < a->Ly; ++y) {
+      const size_t i = (size_t)x * a->Ly + y;
+      orc_equilibrium(rho[i], ux[i], uy[i], T[i], feq);
+      for (int l = 0; l < Q; ++l) d[l * plane(a) + at(a, x, y)] = feq[l];
+    }
+  }
+}
+
 /* ------------------------------------------------ Rayleigh-Taylor initial state */
 
 /* SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): one step of the generator

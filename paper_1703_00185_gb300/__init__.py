@@ -1,0 +1,303 @@
+"""GB300 (sm_103a) thermal D2Q37 lattice Boltzmann step: Python binding.
+
+A thin ``ctypes`` layer over the C ABI declared in ``include/d2q37.h`` and
+built into ``libd2q37_gb300.so`` next to this file.  Functions named
+``lbm_*`` marshal arguments and call the C entry point of the same name;
+:class:`Lattice` bundles them with PyTorch-owned device memory and the
+current PyTorch CUDA stream.  Every step of the method runs in the library's
+CUDA kernels; this module computes nothing itself and raises if the library
+is missing.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+Q = 37
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5
+PHASE_PROPAGATE, PHASE_BC, PHASE_COLLIDE, PHASE_ALL = 1, 2, 4, 7
+KERNEL_SEPARATE, KERNEL_FUSED = 0, 1
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libd2q37_gb300.so")
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (what, lbm_strerror(code) if _lib else "library error", code))
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("g0", ctypes.c_double), ("T_top", ctypes.c_double),
+                ("T_bot", ctypes.c_double), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("periodic_y", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("D2Q37 CUDA library not built (%s missing): run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    pp = ctypes.POINTER(lbm_params)
+    sig = {
+        "lbm_default_params": (None, [pp]),
+        "lbm_velocity_set": (ctypes.c_int, [ip, ip]),
+        "lbm_quadrature": (ctypes.c_int, [dp, dp]),
+        "lbm_required_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, pp]),
+        "lbm_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, pp, ctypes.POINTER(vp)]),
+        "lbm_create_ext": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, pp, vp, ctypes.c_size_t, vp,
+                                          ctypes.POINTER(vp)]),
+        "lbm_init_rayleigh_taylor": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "lbm_set_populations": (ctypes.c_int, [vp, vp]),
+        "lbm_get_populations": (ctypes.c_int, [vp, vp]),
+        "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_run_phases": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+        "lbm_fields": (ctypes.c_int, [vp, vp, vp, vp]),
+        "lbm_fields_device": (ctypes.c_int, [vp, vp, vp, vp]),
+        "lbm_synchronize": (ctypes.c_int, [vp]),
+        "lbm_launch_count": (ctypes.c_int64, [vp]),
+        "lbm_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_kernel_times": (ctypes.c_int, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
+        "lbm_destroy": (None, [vp]),
+        "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the C entry points this binding wraps."""
+    return ["lbm_default_params", "lbm_velocity_set", "lbm_quadrature", "lbm_required_bytes", "lbm_create",
+            "lbm_create_ext", "lbm_init_rayleigh_taylor", "lbm_set_populations", "lbm_get_populations",
+            "lbm_step", "lbm_run_phases", "lbm_fields", "lbm_fields_device", "lbm_synchronize",
+            "lbm_launch_count", "lbm_set_timing", "lbm_kernel_times", "lbm_destroy", "lbm_strerror"]
+
+
+KERNEL_KINDS = ("wrap", "propagate", "bc", "collide", "fused", "fields", "init")
+
+
+def _check(rc, what):
+    if rc != LBM_OK:
+        raise LBMError(rc, what)
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (host or device)."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+# ---------------------------------------------------------------- thin wrappers
+
+def lbm_strerror(code):
+    return load_library().lbm_strerror(code).decode()
+
+
+def lbm_default_params():
+    p = lbm_params()
+    load_library().lbm_default_params(ctypes.byref(p))
+    return p
+
+
+def lbm_velocity_set():
+    cx, cy = (ctypes.c_int * Q)(), (ctypes.c_int * Q)()
+    _check(load_library().lbm_velocity_set(cx, cy), "lbm_velocity_set")
+    return np.array(cx[:]), np.array(cy[:])
+
+
+def lbm_quadrature():
+    s, w = ctypes.c_double(), (ctypes.c_double * Q)()
+    _check(load_library().lbm_quadrature(ctypes.byref(s), w), "lbm_quadrature")
+    return s.value, np.array(w[:])
+
+
+def lbm_required_bytes(Lx, Ly, params):
+    return load_library().lbm_required_bytes(Lx, Ly, ctypes.byref(params))
+
+
+def lbm_create(Lx, Ly, params):
+    h = ctypes.c_void_p()
+    _check(load_library().lbm_create(Lx, Ly, ctypes.byref(params), ctypes.byref(h)), "lbm_create")
+    return h
+
+
+def lbm_create_ext(Lx, Ly, params, dev_ptr, nbytes, cuda_stream):
+    h = ctypes.c_void_p()
+    _check(load_library().lbm_create_ext(Lx, Ly, ctypes.byref(params), dev_ptr, nbytes, cuda_stream,
+                                         ctypes.byref(h)), "lbm_create_ext")
+    return h
+
+
+def lbm_init_rayleigh_taylor(h, seed):
+    _check(load_library().lbm_init_rayleigh_taylor(h, seed), "lbm_init_rayleigh_taylor")
+
+
+def lbm_set_populations(h, f):
+    _check(load_library().lbm_set_populations(h, _ptr(f)), "lbm_set_populations")
+
+
+def lbm_get_populations(h, f):
+    _check(load_library().lbm_get_populations(h, _ptr(f)), "lbm_get_populations")
+
+
+def lbm_step(h, n):
+    _check(load_library().lbm_step(h, n), "lbm_step")
+
+
+def lbm_run_phases(h, n, phases):
+    _check(load_library().lbm_run_phases(h, n, phases), "lbm_run_phases")
+
+
+def lbm_fields(h, rho, u, T):
+    _check(load_library().lbm_fields(h, _ptr(rho), _ptr(u), _ptr(T)), "lbm_fields")
+
+
+def lbm_fields_device(h, rho, u, T):
+    _check(load_library().lbm_fields_device(h, _ptr(rho), _ptr(u), _ptr(T)), "lbm_fields_device")
+
+
+def lbm_synchronize(h):
+    _check(load_library().lbm_synchronize(h), "lbm_synchronize")
+
+
+def lbm_launch_count(h):
+    return load_library().lbm_launch_count(h)
+
+
+def lbm_set_timing(h, enable):
+    _check(load_library().lbm_set_timing(h, int(bool(enable))), "lbm_set_timing")
+
+
+def lbm_kernel_times(h):
+    """{kind: (total_ms, launches)} since timing was enabled."""
+    n = len(KERNEL_KINDS)
+    ms, cnt = (ctypes.c_double * n)(), (ctypes.c_int64 * n)()
+    _check(load_library().lbm_kernel_times(h, ms, cnt), "lbm_kernel_times")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def lbm_destroy(h):
+    load_library().lbm_destroy(h)
+
+
+# ------------------------------------------------------------------ Lattice
+
+class Lattice:
+    """One Lx x Ly lattice on a CUDA device, memory owned by PyTorch.
+
+    ``kernel`` is "fused" (pbc + one propagate/bc/collide kernel per step) or
+    "separate" (pbc, propagate, bc, collide).  All work runs on ``stream``
+    (default: the current PyTorch stream of ``device``)."""
+
+    def __init__(self, Lx, Ly, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5, kernel="fused", periodic_y=False,
+                 device=None, stream=None):
+        import torch
+        self._torch = torch
+        load_library()
+        self.Lx, self.Ly = int(Lx), int(Ly)
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        p = lbm_default_params()
+        p.tau, p.g0, p.T_top, p.T_bot = tau, g0, T_top, T_bot
+        p.kernel = {"fused": KERNEL_FUSED, "separate": KERNEL_SEPARATE}[kernel]
+        p.periodic_y = int(bool(periodic_y))
+        self.params = p
+        nbytes = lbm_required_bytes(self.Lx, self.Ly, p)
+        if nbytes == 0:
+            raise LBMError(LBM_EINVAL, "lbm_required_bytes")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self._mem = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self._h = lbm_create_ext(self.Lx, self.Ly, p, self._mem.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    # every call runs with this lattice's device current
+    def _dev(self):
+        return self._torch.cuda.device(self.device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            with self._dev():
+                lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_rayleigh_taylor(self, seed):
+        with self._dev():
+            lbm_init_rayleigh_taylor(self._h, seed)
+
+    def step(self, n=1):
+        with self._dev():
+            lbm_step(self._h, n)
+
+    def run_phases(self, n, phases):
+        with self._dev():
+            lbm_run_phases(self._h, n, phases)
+
+    def set_populations(self, f):
+        """f: [37, Lx, Ly] float64 host array (numpy or pinned torch) in library order."""
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+        assert tuple(f.shape) == (Q, self.Lx, self.Ly)
+        with self._dev():
+            lbm_set_populations(self._h, f)
+            if isinstance(f, np.ndarray):
+                lbm_synchronize(self._h)
+
+    def populations(self, out=None):
+        f = out if out is not None else np.empty((Q, self.Lx, self.Ly))
+        with self._dev():
+            lbm_get_populations(self._h, f)
+        return f
+
+    def fields(self, out=None):
+        """(rho[Lx, Ly], u[2, Lx, Ly], T[Lx, Ly]) as host float64 arrays."""
+        if out is None:
+            out = (np.empty((self.Lx, self.Ly)), np.empty((2, self.Lx, self.Ly)), np.empty((self.Lx, self.Ly)))
+        with self._dev():
+            lbm_fields(self._h, *out)
+        return out
+
+    def fields_device(self):
+        """(rho, u, T) as float64 torch tensors on the device (asynchronous)."""
+        t = self._torch
+        rho = t.empty((self.Lx, self.Ly), dtype=t.float64, device=self.device)
+        u = t.empty((2, self.Lx, self.Ly), dtype=t.float64, device=self.device)
+        T = t.empty((self.Lx, self.Ly), dtype=t.float64, device=self.device)
+        with self._dev():
+            lbm_fields_device(self._h, rho, u, T)
+        return rho, u, T
+
+    def synchronize(self):
+        with self._dev():
+            lbm_synchronize(self._h)
+
+    @property
+    def launch_count(self):
+        return lbm_launch_count(self._h)
+
+    def set_timing(self, enable=True):
+        with self._dev():
+            lbm_set_timing(self._h, enable)
+
+    def kernel_times(self):
+        with self._dev():
+            return lbm_kernel_times(self._h)

@@ -1,0 +1,462 @@
+// C ABI of the D2Q37 library (declared in include/d2q37.h): handle life
+// cycle, device memory layout, step scheduling and host<->device transfers.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/d2q37.h"
+#include "d2q37_launch.h"
+
+using namespace d2q37;
+
+struct lbm_t {
+  int Lx, Ly, NX, NY;
+  lbm_params prm;
+  StepParams sp;
+  double* buf[2];
+  int cur;
+  double* scratch;  // 4 Lx Ly doubles: fields, or the initial temperature
+  void* owned;      // cudaMalloc'ed block, NULL for lbm_create_ext
+  cudaStream_t stream;
+  bool owns_stream;
+  bool have_state;
+  int64_t launches;
+  // per-kernel timing: event pairs recorded around launches, folded into the
+  // totals when the stream is synchronised
+  bool timing;
+  struct Pending {
+    int kind;
+    cudaEvent_t start, stop;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double kind_ms[LBM_KIND_COUNT];
+  int64_t kind_launches[LBM_KIND_COUNT];
+};
+
+namespace {
+
+std::once_flag g_quad_once;
+bool g_quad_ok = false;
+ShellConsts g_consts;
+std::mutex g_dev_mutex;
+bool g_dev_ready[256];
+
+void solve_once() {
+  double s, w[kShells];
+  if (!solve_quadrature(&s, w)) return;
+  ShellConsts& c = g_consts;
+  c.s = s;
+  c.s2 = s * s;
+  for (int k = 0; k < kShells; ++k) {
+    const double x2 = c.s2 * shell_c2(k);
+    c.w[k] = w[k];
+    c.alpha[k] = (x2 - 2.0) / 2.0;
+    c.beta[k] = (4.0 - x2) / 4.0;
+    c.gamma[k] = (x2 * x2 - 8.0 * x2 + 8.0) / 8.0;
+    c.delta[k] = (x2 - 4.0) / 2.0;
+    c.eps[k] = (x2 - 6.0) / 4.0;
+  }
+  g_quad_ok = true;
+}
+
+bool quadrature_ready() {
+  std::call_once(g_quad_once, solve_once);
+  return g_quad_ok;
+}
+
+int ensure_device_consts() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return LBM_ECUDA;
+  std::lock_guard<std::mutex> lock(g_dev_mutex);
+  if (!g_dev_ready[dev]) {
+    if (upload_shell_consts(g_consts) != cudaSuccess) return LBM_ECUDA;
+    g_dev_ready[dev] = true;
+  }
+  return LBM_OK;
+}
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+int frame_ny(int Ly) { return ((Ly + 2 * kHy) + 15) / 16 * 16; }
+
+bool valid_params(int Lx, int Ly, const lbm_params* p) {
+  if (!p || Lx < 3 || Ly < 6) return false;
+  if (!(p->tau > 0.5) || !std::isfinite(p->tau) || !std::isfinite(p->g0)) return false;
+  if (!(p->T_top > 0.0) || !(p->T_bot > 0.0)) return false;
+  if (p->precision != 0) return false;
+  if (p->kernel != LBM_KERNEL_SEPARATE && p->kernel != LBM_KERNEL_FUSED) return false;
+  if ((long long)Lx * Ly > (1LL << 34)) return false;
+  return true;
+}
+
+size_t buffer_bytes(int Lx, int Ly) {
+  return align256((size_t)kQ * (size_t)(Lx + 2 * kHx) * (size_t)frame_ny(Ly) * sizeof(double));
+}
+
+size_t scratch_bytes(int Lx, int Ly) { return align256((size_t)4 * Lx * Ly * sizeof(double)); }
+
+void fill_step_params(lbm_t* h) {
+  StepParams& sp = h->sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.Lx = h->Lx;
+  sp.Ly = h->Ly;
+  sp.NY = h->NY;
+  sp.periodic_y = h->prm.periodic_y ? 1 : 0;
+  sp.plane = (long long)h->NX * h->NY;
+  const double tau = h->prm.tau;
+  sp.omega = 1.0 / tau;
+  sp.one_minus_omega = 1.0 - sp.omega;
+  const double gy = -h->prm.g0;
+  sp.uy_shift = tau * gy;
+  sp.theta_shift = -(tau * tau * gy * gy) / 2.0 - 1.0;
+  const double Tw[2] = {h->prm.T_bot, h->prm.T_top};
+  for (int wall = 0; wall < 2; ++wall) {
+    equilibrium(g_consts, 1.0, 0.0, 0.0, Tw[wall], sp.fw[wall]);
+    double den = 0.0;
+    for (int r = 0; r < 3; ++r)
+      for (int l = 0; l < kQ; ++l) {
+        const bool missing = wall ? (kCy[l] < -r) : (kCy[l] > r);
+        if (missing) den += sp.fw[wall][l];
+      }
+    sp.inv_denom[wall] = 1.0 / den;
+  }
+}
+
+int check(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
+
+cudaEvent_t pooled_event(lbm_t* h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Enqueue one launcher; with timing on, bracket it with an event pair.
+template <typename F>
+int run_kernel(lbm_t* h, int kind, F&& launcher) {
+  cudaEvent_t start = nullptr, stop = nullptr;
+  if (h->timing) {
+    start = pooled_event(h);
+    stop = pooled_event(h);
+    if (!start || !stop || cudaEventRecord(start, h->stream) != cudaSuccess) return LBM_ECUDA;
+  }
+  const int n = launcher();
+  if (n < 0) return LBM_ECUDA;
+  h->launches += n;
+  if (h->timing) {
+    if (cudaEventRecord(stop, h->stream) != cudaSuccess) return LBM_ECUDA;
+    h->pending.push_back({kind, start, stop});
+    h->kind_launches[kind] += n;
+  }
+  return LBM_OK;
+}
+
+// Fold recorded event pairs into the per-kind totals (stream already synced).
+int drain_timing(lbm_t* h) {
+  int rc = LBM_OK;
+  for (auto& p : h->pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.start, p.stop) != cudaSuccess) rc = LBM_ECUDA;
+    h->kind_ms[p.kind] += ms;
+    h->event_pool.push_back(p.start);
+    h->event_pool.push_back(p.stop);
+  }
+  h->pending.clear();
+  return rc;
+}
+
+int setup_handle(lbm_t* h, int Lx, int Ly, const lbm_params* p, void* mem, cudaStream_t stream) {
+  h->Lx = Lx;
+  h->Ly = Ly;
+  h->NX = Lx + 2 * kHx;
+  h->NY = frame_ny(Ly);
+  h->prm = *p;
+  const size_t bb = buffer_bytes(Lx, Ly);
+  char* base = (char*)mem;
+  h->buf[0] = (double*)base;
+  h->buf[1] = (double*)(base + bb);
+  h->scratch = (double*)(base + 2 * bb);
+  h->cur = 0;
+  h->stream = stream;
+  fill_step_params(h);
+  // halo rows must read as zero: the pull takes the populations a wall
+  // replaces from there
+  int rc = check(cudaMemsetAsync(base, 0, 2 * bb, stream));
+  if (rc == LBM_OK) rc = check(cudaStreamSynchronize(stream));
+  return rc;
+}
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the finaliser applied to
+// state v + 0x9e3779b97f4a7c15.
+uint64_t splitmix64(uint64_t v) {
+  uint64_t z = v + 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+int step_once(lbm_t* h, int phases, bool fused) {
+  double* src = h->buf[h->cur];
+  double* dst = h->buf[1 - h->cur];
+  int rc = LBM_OK;
+  if (phases & LBM_PHASE_PROPAGATE) {
+    rc = run_kernel(h, LBM_KIND_WRAP, [&] { return launch_wrap(src, h->sp, h->stream); });
+    if (rc) return rc;
+    if (fused) {
+      rc = run_kernel(h, LBM_KIND_FUSED, [&] { return launch_fused(src, dst, h->sp, h->stream); });
+      if (rc) return rc;
+      h->cur = 1 - h->cur;
+      return LBM_OK;
+    }
+    rc = run_kernel(h, LBM_KIND_PROPAGATE, [&] { return launch_propagate(src, dst, h->sp, h->stream); });
+    if (rc) return rc;
+    if ((phases & LBM_PHASE_BC) && !h->prm.periodic_y) {
+      rc = run_kernel(h, LBM_KIND_BC, [&] { return launch_bc(src, dst, h->sp, h->stream); });
+      if (rc) return rc;
+    }
+    h->cur = 1 - h->cur;
+  }
+  if (phases & LBM_PHASE_COLLIDE)
+    rc = run_kernel(h, LBM_KIND_COLLIDE, [&] { return launch_collide(h->buf[h->cur], h->sp, h->stream); });
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_params(lbm_params* p) {
+  if (!p) return;
+  p->tau = 0.8;
+  p->g0 = 1e-4;
+  p->T_top = 0.5;
+  p->T_bot = 1.5;
+  p->precision = 0;
+  p->kernel = LBM_KERNEL_FUSED;
+  p->periodic_y = 0;
+}
+
+int lbm_velocity_set(int* cx, int* cy) {
+  if (!cx || !cy) return LBM_EINVAL;
+  for (int l = 0; l < kQ; ++l) {
+    cx[l] = kCx[l];
+    cy[l] = kCy[l];
+  }
+  return LBM_OK;
+}
+
+int lbm_quadrature(double* s, double* w) {
+  if (!s || !w) return LBM_EINVAL;
+  if (!quadrature_ready()) return LBM_ESTATE;
+  *s = g_consts.s;
+  for (int l = 0; l < kQ; ++l) w[l] = g_consts.w[kShellOf[l]];
+  return LBM_OK;
+}
+
+size_t lbm_required_bytes(int Lx, int Ly, const lbm_params* p) {
+  if (!valid_params(Lx, Ly, p)) return 0;
+  return 2 * buffer_bytes(Lx, Ly) + scratch_bytes(Lx, Ly);
+}
+
+int lbm_create(int Lx, int Ly, const lbm_params* p, lbm_t** out) {
+  if (!out || !valid_params(Lx, Ly, p)) return LBM_EINVAL;
+  if (!quadrature_ready()) return LBM_ESTATE;
+  int rc = ensure_device_consts();
+  if (rc) return rc;
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, lbm_required_bytes(Lx, Ly, p)) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ENOMEM;
+  }
+  cudaStream_t stream;
+  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFree(mem);
+    return LBM_ECUDA;
+  }
+  lbm_t* h = new lbm_t();
+  h->owned = mem;
+  h->owns_stream = true;
+  rc = setup_handle(h, Lx, Ly, p, mem, stream);
+  if (rc) {
+    lbm_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_create_ext(int Lx, int Ly, const lbm_params* p, void* dev_buf, size_t bytes, void* cuda_stream,
+                   lbm_t** out) {
+  if (!out || !dev_buf || !valid_params(Lx, Ly, p)) return LBM_EINVAL;
+  if (((uintptr_t)dev_buf & 255) != 0) return LBM_EINVAL;
+  if (bytes < lbm_required_bytes(Lx, Ly, p)) return LBM_ENOMEM;
+  if (!quadrature_ready()) return LBM_ESTATE;
+  int rc = ensure_device_consts();
+  if (rc) return rc;
+  lbm_t* h = new lbm_t();
+  h->owned = nullptr;
+  h->owns_stream = false;
+  rc = setup_handle(h, Lx, Ly, p, dev_buf, (cudaStream_t)cuda_stream);
+  if (rc) {
+    lbm_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_init_rayleigh_taylor(lbm_t* h, uint64_t seed) {
+  if (!h) return LBM_EINVAL;
+  const int Lx = h->Lx, Ly = h->Ly;
+  std::vector<double> T((size_t)Lx * Ly);
+  const double Tt = h->prm.T_top, Tb = h->prm.T_bot;
+  for (int x = 0; x < Lx; ++x) {
+    const double arg = (2.0 * M_PI * ((double)x + 0.5)) / (double)Lx;
+    const double yi = 0.5 * (double)Ly + ((double)Ly / 64.0) * std::sin(arg);
+    for (int y = 0; y < Ly; ++y) {
+      const double T0 = ((double)y + 0.5 < yi) ? Tb : Tt;
+      const uint64_t r = splitmix64(seed + (uint64_t)x * (uint64_t)Ly + (uint64_t)y);
+      const double U = (double)(r >> 11) * 0x1.0p-53;
+      T[(size_t)x * Ly + y] = T0 * (1.0 + 1e-3 * (2.0 * U - 1.0));
+    }
+  }
+  int rc = check(cudaMemcpyAsync(h->scratch, T.data(), T.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                 h->stream));
+  if (!rc) rc = check(cudaMemsetAsync(h->buf[h->cur], 0, buffer_bytes(Lx, Ly), h->stream));
+  if (!rc)
+    rc = run_kernel(h, LBM_KIND_INIT,
+                    [&] { return launch_init_equilibrium(h->buf[h->cur], h->scratch, h->sp, h->stream); });
+  if (!rc) rc = check(cudaStreamSynchronize(h->stream));
+  if (!rc) h->have_state = true;
+  return rc;
+}
+
+int lbm_set_populations(lbm_t* h, const double* f) {
+  if (!h || !f) return LBM_EINVAL;
+  double* d = h->buf[h->cur];
+  for (int l = 0; l < kQ; ++l) {
+    const cudaError_t e = cudaMemcpy2DAsync(d + l * h->sp.plane + (size_t)kHx * h->NY + kHy, h->NY * sizeof(double),
+                                            f + (size_t)l * h->Lx * h->Ly, h->Ly * sizeof(double),
+                                            h->Ly * sizeof(double), h->Lx, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return LBM_ECUDA;
+  }
+  h->have_state = true;
+  return LBM_OK;
+}
+
+int lbm_get_populations(lbm_t* h, double* f) {
+  if (!h || !f) return LBM_EINVAL;
+  if (!h->have_state) return LBM_ESTATE;
+  const double* d = h->buf[h->cur];
+  for (int l = 0; l < kQ; ++l) {
+    const cudaError_t e = cudaMemcpy2DAsync(f + (size_t)l * h->Lx * h->Ly, h->Ly * sizeof(double),
+                                            d + l * h->sp.plane + (size_t)kHx * h->NY + kHy, h->NY * sizeof(double),
+                                            h->Ly * sizeof(double), h->Lx, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return LBM_ECUDA;
+  }
+  return check(cudaStreamSynchronize(h->stream));
+}
+
+int lbm_step(lbm_t* h, int n) {
+  if (!h || n < 0) return LBM_EINVAL;
+  if (!h->have_state) return LBM_ESTATE;
+  const bool fused = h->prm.kernel == LBM_KERNEL_FUSED;
+  for (int t = 0; t < n; ++t) {
+    const int rc = step_once(h, LBM_PHASE_ALL, fused);
+    if (rc) return rc;
+  }
+  return LBM_OK;
+}
+
+int lbm_run_phases(lbm_t* h, int n, int phases) {
+  if (!h || n < 0 || phases <= 0 || phases > LBM_PHASE_ALL) return LBM_EINVAL;
+  if ((phases & LBM_PHASE_BC) && !(phases & LBM_PHASE_PROPAGATE)) return LBM_EINVAL;
+  if (!h->have_state) return LBM_ESTATE;
+  for (int t = 0; t < n; ++t) {
+    const int rc = step_once(h, phases, false);
+    if (rc) return rc;
+  }
+  return LBM_OK;
+}
+
+int lbm_fields_device(lbm_t* h, double* rho, double* u, double* T) {
+  if (!h || !rho || !u || !T) return LBM_EINVAL;
+  if (!h->have_state) return LBM_ESTATE;
+  return run_kernel(h, LBM_KIND_FIELDS, [&] { return launch_fields(h->buf[h->cur], rho, u, T, h->sp, h->stream); });
+}
+
+int lbm_fields(lbm_t* h, double* rho, double* u, double* T) {
+  if (!h || !rho || !u || !T) return LBM_EINVAL;
+  const size_t n = (size_t)h->Lx * h->Ly;
+  double* s = h->scratch;
+  int rc = lbm_fields_device(h, s, s + n, s + 3 * n);
+  if (rc) return rc;
+  rc = check(cudaMemcpyAsync(rho, s, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (!rc) rc = check(cudaMemcpyAsync(u, s + n, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (!rc) rc = check(cudaMemcpyAsync(T, s + 3 * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (!rc) rc = check(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+int lbm_synchronize(lbm_t* h) {
+  if (!h) return LBM_EINVAL;
+  return check(cudaStreamSynchronize(h->stream));
+}
+
+int64_t lbm_launch_count(const lbm_t* h) { return h ? h->launches : 0; }
+
+int lbm_set_timing(lbm_t* h, int enable) {
+  if (!h) return LBM_EINVAL;
+  int rc = check(cudaStreamSynchronize(h->stream));
+  if (drain_timing(h) != LBM_OK) rc = LBM_ECUDA;
+  for (int k = 0; k < LBM_KIND_COUNT; ++k) {
+    h->kind_ms[k] = 0.0;
+    h->kind_launches[k] = 0;
+  }
+  h->timing = enable != 0;
+  return rc;
+}
+
+int lbm_kernel_times(lbm_t* h, double* ms, int64_t* launches) {
+  if (!h) return LBM_EINVAL;
+  int rc = check(cudaStreamSynchronize(h->stream));
+  if (drain_timing(h) != LBM_OK) rc = LBM_ECUDA;
+  for (int k = 0; k < LBM_KIND_COUNT; ++k) {
+    if (ms) ms[k] = h->kind_ms[k];
+    if (launches) launches[k] = h->kind_launches[k];
+  }
+  return rc;
+}
+
+void lbm_destroy(lbm_t* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drain_timing(h);
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  if (h->owns_stream && h->stream) cudaStreamDestroy(h->stream);
+  if (h->owned) cudaFree(h->owned);
+  delete h;
+}
+
+const char* lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "success";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of device memory or caller buffer too small";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_ETIMEOUT: return "bounded device wait timed out";
+    case LBM_ESTATE: return "call out of order (no state yet, or quadrature unavailable)";
+    default: return "unknown error code";
+  }
+}
+
+}  // extern "C"

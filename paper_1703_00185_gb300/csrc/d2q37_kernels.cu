@@ -1,0 +1,308 @@
+// sm_103a kernels of one thermal D2Q37 time step, FP64 populations.
+//
+// Layout (Sec. "Data Structure Analysis"): structure of arrays, one plane per
+// population, each plane column-major in y (y contiguous), in a halo frame of
+// (Lx + 2*3) columns by NY rows, physical site (x, y) at
+// (x + 3) * NY + (y + 16).  NY = Ly + 32 rounded up to a multiple of 16, so every
+// column starts on a 128-byte boundary.  Two frames are double-buffered.
+//
+// Kernels and the step sequence (Sec. "Code Organization"):
+//   wrap      pbc: fill the 3-column x halos (and y halos when y is periodic)
+//   propagate pull form of Eq. master2: dst_l(x,y) = src_l(x - c_lx, y - c_ly)
+//   bc        diffuse walls on rows 0..2 and Ly-3..Ly-1
+//   collide   BGK relaxation (Eq. discrete) to the shifted equilibrium of
+//             Eq. MASTERSHIFT3, in place on dst
+//   fused     propagate + bc + collide in one pass, src -> dst
+//
+// Threads: one per lattice site, blocks of 128 consecutive y of one column
+// (the paper's 1-D blocks along y, Sec. "The propagate and bc Kernels").
+// Every warp reads 32 consecutive doubles of each population plane, so each
+// gather is a coalesced 256-byte row shifted by at most 3 elements.
+#include <cuda_runtime.h>
+
+#include "d2q37_launch.h"
+
+namespace d2q37 {
+
+__constant__ ShellConsts c_shell;
+
+namespace {
+
+constexpr int kBlockY = 128;
+
+__device__ __forceinline__ long long site_index(const StepParams& p, int x, int y) {
+  return (long long)(x + kHx) * p.NY + (y + kHy);
+}
+
+// rho, u and T of one site (Sec. "Lattice Boltzmann methods"):
+// rho = sum f, rho u = s sum c f, D rho T = sum |xi|^2 f - rho |u|^2 (D = 2),
+// the last being sum |xi - u|^2 f expanded.  Pair sums and differences carry
+// the even and odd moments.
+__device__ __forceinline__ void site_moments(const double (&f)[kQ], double& rho, double& ux, double& uy,
+                                             double& T) {
+  double sh[kShells];
+  sh[0] = f[0];
+#pragma unroll
+  for (int k = 1; k < kShells; ++k) sh[k] = 0.0;
+  double jx = 0.0, jy = 0.0;
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    const double sum = f[1 + 2 * p] + f[2 + 2 * p];
+    const double dif = f[1 + 2 * p] - f[2 + 2 * p];
+    sh[pair_shell(p)] += sum;
+    if (pair_cx(p) != 0) jx += (double)pair_cx(p) * dif;
+    if (pair_cy(p) != 0) jy += (double)pair_cy(p) * dif;
+  }
+  rho = sh[0];
+  double e = 0.0;
+#pragma unroll
+  for (int k = 1; k < kShells; ++k) {
+    rho += sh[k];
+    e += (double)shell_c2(k) * sh[k];
+  }
+  const double inv_rho = 1.0 / rho;
+  ux = c_shell.s * jx * inv_rho;
+  uy = c_shell.s * jy * inv_rho;
+  T = 0.5 * (c_shell.s2 * e * inv_rho - (ux * ux + uy * uy));
+}
+
+// BGK collision of one site, f <- f - (f - f^eq(rho, u_bar, T_bar)) / tau with
+// u_bar = u + tau g, T_bar = T - tau^2 g^2 / D (Eq. MASTERSHIFT3, Eq. discrete).
+// The equilibrium is evaluated per pair as even +- odd parts with per-shell
+// coefficients (see ShellConsts), pre-scaled by omega rho w_shell.
+__device__ __forceinline__ void collide_site(double (&f)[kQ], const StepParams& p) {
+  double rho, ux, uy, T;
+  site_moments(f, rho, ux, uy, T);
+  const double ubx = ux;
+  const double uby = uy + p.uy_shift;
+  const double q = ubx * ubx + uby * uby;
+  const double th = T + p.theta_shift;
+  const double A0 = 1.0 + q * (-0.5 + 0.125 * q);
+  const double B1 = 1.0 - 0.5 * q;
+  const double B2 = 0.5 - 0.25 * q;
+  const double sux = c_shell.s * ubx, suy = c_shell.s * uby;
+  const double wr = p.omega * rho;
+  const double keep = p.one_minus_omega;
+  {
+    const double C0 = A0 + th * (c_shell.alpha[0] + q * c_shell.beta[0] + th * c_shell.gamma[0]);
+    f[0] = fma(keep, f[0], wr * c_shell.w[0] * C0);
+  }
+#pragma unroll
+  for (int k = 1; k < kShells; ++k) {
+    const double W = wr * c_shell.w[k];
+    const double P0 = W * (A0 + th * (c_shell.alpha[k] + q * c_shell.beta[k] + th * c_shell.gamma[k]));
+    const double P1 = W * (B1 + th * c_shell.delta[k]);
+    const double P2 = W * (B2 + th * c_shell.eps[k]);
+    const double P3 = W * (1.0 / 6.0);
+    const double P4 = W * (1.0 / 24.0);
+#pragma unroll
+    for (int pr = 0; pr < kPairs; ++pr) {
+      if (pair_shell(pr) != k) continue;
+      const double a = (double)pair_cx(pr) * sux + (double)pair_cy(pr) * suy;
+      const double b = a * a;
+      const double even = P0 + b * (P2 + b * P4);
+      const double odd = a * (P1 + b * P3);
+      f[1 + 2 * pr] = fma(keep, f[1 + 2 * pr], even + odd);
+      f[2 + 2 * pr] = fma(keep, f[2 + 2 * pr], even - odd);
+    }
+  }
+}
+
+// Wall bc for a site of a wall band, applied to its gathered populations:
+// rows r = 0..2 from the wall; a population is missing when the pull took it
+// from beyond the wall, outgoing when it leaves the column past the wall.
+// Missing ones become rho_w f^eq_l(1, 0, T_wall), rho_w = outgoing mass of the
+// column / sum of f^eq over the missing pairs, so the wall injects exactly the
+// mass that left through it (reading of Sec. "The propagate and bc Kernels").
+__device__ __forceinline__ double wall_density(const double* __restrict__ src, const StepParams& p, int x,
+                                               int wall) {
+  double out = 0.0;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int y = wall ? p.Ly - 1 - r : r;
+    const long long i = site_index(p, x, y);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const int cy = vel_cy(l);
+      if (wall ? (cy > r) : (cy < -r)) out += src[l * p.plane + i];
+    }
+  }
+  return out * p.inv_denom[wall];
+}
+
+__global__ void __launch_bounds__(256) wrap_kernel(double* __restrict__ buf, StepParams p) {
+  const int rows_a = p.periodic_y ? p.Ly + 2 * kHx : p.Ly;
+  const int y0 = p.periodic_y ? -kHx : 0;
+  const long long n_a = (long long)kQ * 6 * rows_a;
+  const long long n_b = p.periodic_y ? (long long)kQ * p.Lx * 6 : 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n_a + n_b;
+       t += (long long)gridDim.x * blockDim.x) {
+    int l, xd, yd, xs, ys;
+    if (t < n_a) {  // x halo columns, whole height (corners included when y is periodic)
+      const int yy = (int)(t % rows_a);
+      const int h = (int)((t / rows_a) % 6);
+      l = (int)(t / (6LL * rows_a));
+      xd = h < 3 ? h - 3 : p.Lx + h - 3;
+      xs = h < 3 ? p.Lx + h - 3 : h - 3;
+      yd = y0 + yy;
+      ys = yd < 0 ? yd + p.Ly : (yd >= p.Ly ? yd - p.Ly : yd);
+    } else {  // y halo rows of the physical columns (periodic y only)
+      const long long u = t - n_a;
+      const int r = (int)(u % 6);
+      xd = (int)((u / 6) % p.Lx);
+      l = (int)(u / (6LL * p.Lx));
+      xs = xd;
+      yd = r < 3 ? r - 3 : p.Ly + r - 3;
+      ys = r < 3 ? p.Ly + r - 3 : r - 3;
+    }
+    buf[l * p.plane + site_index(p, xd, yd)] = buf[l * p.plane + site_index(p, xs, ys)];
+  }
+}
+
+__global__ void __launch_bounds__(kBlockY) propagate_kernel(const double* __restrict__ src,
+                                                            double* __restrict__ dst, StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  const long long i = site_index(p, x, y);
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) dst[l * p.plane + i] = src[l * p.plane + i - vel_cx(l) * p.NY - vel_cy(l)];
+}
+
+__global__ void __launch_bounds__(128) bc_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                                 StepParams p) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * p.Lx) return;
+  const int wall = t >= p.Lx;
+  const int x = t - wall * p.Lx;
+  const double rho_w = wall_density(src, p, x, wall);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int y = wall ? p.Ly - 1 - r : r;
+    const long long i = site_index(p, x, y);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const int cy = vel_cy(l);
+      if (wall ? (cy < -r) : (cy > r)) dst[l * p.plane + i] = rho_w * p.fw[wall][l];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlockY) collide_kernel(double* __restrict__ buf, StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  const long long i = site_index(p, x, y);
+  double f[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) f[l] = buf[l * p.plane + i];
+  collide_site(f, p);
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) buf[l * p.plane + i] = f[l];
+}
+
+__global__ void __launch_bounds__(kBlockY) fused_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                                        StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  const long long i = site_index(p, x, y);
+  double f[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) f[l] = src[l * p.plane + i - vel_cx(l) * p.NY - vel_cy(l)];
+  if (!p.periodic_y && (y < 3 || y >= p.Ly - 3)) {
+    const int wall = y >= p.Ly - 3;
+    const int r = wall ? p.Ly - 1 - y : y;
+    const double rho_w = wall_density(src, p, x, wall);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const int cy = vel_cy(l);
+      if (wall ? (cy < -r) : (cy > r)) f[l] = rho_w * p.fw[wall][l];
+    }
+  }
+  collide_site(f, p);
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) dst[l * p.plane + i] = f[l];
+}
+
+__global__ void __launch_bounds__(kBlockY) fields_kernel(const double* __restrict__ buf, double* __restrict__ rho,
+                                                         double* __restrict__ u, double* __restrict__ T,
+                                                         StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  const long long i = site_index(p, x, y);
+  double f[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) f[l] = buf[l * p.plane + i];
+  double r, ux, uy, t;
+  site_moments(f, r, ux, uy, t);
+  const long long o = (long long)x * p.Ly + y;
+  const long long n = (long long)p.Lx * p.Ly;
+  rho[o] = r;
+  u[o] = ux;
+  u[n + o] = uy;
+  T[o] = t;
+}
+
+__global__ void __launch_bounds__(kBlockY) init_equilibrium_kernel(double* __restrict__ buf,
+                                                                   const double* __restrict__ T, StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  const double t = T[(long long)x * p.Ly + y];
+  double feq[kQ];
+  equilibrium(c_shell, 1.0 / t, 0.0, 0.0, t, feq);
+  const long long i = site_index(p, x, y);
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) buf[l * p.plane + i] = feq[l];
+}
+
+dim3 site_grid(const StepParams& p) { return dim3(p.Lx, (p.Ly + kBlockY - 1) / kBlockY); }
+
+int done(int n) { return cudaGetLastError() == cudaSuccess ? n : -1; }
+
+}  // namespace
+
+cudaError_t upload_shell_consts(const ShellConsts& c) { return cudaMemcpyToSymbol(c_shell, &c, sizeof(c)); }
+
+int launch_wrap(double* buf, const StepParams& p, cudaStream_t stream) {
+  const long long n = (long long)kQ * 6 * (p.periodic_y ? p.Ly + 2 * kHx : p.Ly) +
+                      (p.periodic_y ? (long long)kQ * p.Lx * 6 : 0);
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  wrap_kernel<<<(unsigned)blocks, 256, 0, stream>>>(buf, p);
+  return done(1);
+}
+
+int launch_propagate(const double* src, double* dst, const StepParams& p, cudaStream_t stream) {
+  propagate_kernel<<<site_grid(p), kBlockY, 0, stream>>>(src, dst, p);
+  return done(1);
+}
+
+int launch_bc(const double* src, double* dst, const StepParams& p, cudaStream_t stream) {
+  bc_kernel<<<(2 * p.Lx + 127) / 128, 128, 0, stream>>>(src, dst, p);
+  return done(1);
+}
+
+int launch_collide(double* buf, const StepParams& p, cudaStream_t stream) {
+  collide_kernel<<<site_grid(p), kBlockY, 0, stream>>>(buf, p);
+  return done(1);
+}
+
+int launch_fused(const double* src, double* dst, const StepParams& p, cudaStream_t stream) {
+  fused_kernel<<<site_grid(p), kBlockY, 0, stream>>>(src, dst, p);
+  return done(1);
+}
+
+int launch_fields(const double* buf, double* rho, double* u, double* T, const StepParams& p, cudaStream_t stream) {
+  fields_kernel<<<site_grid(p), kBlockY, 0, stream>>>(buf, rho, u, T, p);
+  return done(1);
+}
+
+int launch_init_equilibrium(double* buf, const double* T, const StepParams& p, cudaStream_t stream) {
+  init_equilibrium_kernel<<<site_grid(p), kBlockY, 0, stream>>>(buf, T, p);
+  return done(1);
+}
+
+}  // namespace d2q37

@@ -1,0 +1,142 @@
+// D2Q37 lattice description and the per-site FP64 arithmetic shared by the
+// kernels of this library (host and device).
+//
+// Velocity set (reading of Sec. "Lattice Boltzmann methods"; the paper labels
+// populations arbitrarily): every integer hop c with |c|^2 <= 10, 37 vectors
+// in 8 shells.  This library orders them as the rest population followed by
+// 18 pairs (c, -c), pairs grouped by shell, so that the even and odd parts of
+// the equilibrium are shared inside a pair.
+#pragma once
+
+#include <cstdint>
+
+namespace d2q37 {
+
+constexpr int kQ = 37;
+constexpr int kPairs = 18;
+constexpr int kShells = 8;
+constexpr int kHx = 3;   // halo columns: populations move at most 3 sites (Sec. "Data Structure Analysis")
+constexpr int kHy = 16;  // halo rows: 16 doubles = 128 B keeps every column 128-byte aligned
+
+// Population l = 0 is the rest population; pair p has l = 1 + 2p for +c and
+// l = 2 + 2p for -c.
+__host__ __device__ constexpr int pair_cx(int p) {
+  switch (p) {
+    case 0: return 1;  case 1: return 0;                      // shell |c|^2 = 1
+    case 2: return 1;  case 3: return 1;                      // 2
+    case 4: return 2;  case 5: return 0;                      // 4
+    case 6: return 2;  case 7: return 2;  case 8: return 1;  case 9: return 1;   // 5
+    case 10: return 2; case 11: return 2;                     // 8
+    case 12: return 3; case 13: return 0;                     // 9
+    case 14: return 3; case 15: return 3; case 16: return 1; case 17: return 1;  // 10
+    default: return 0;
+  }
+}
+
+__host__ __device__ constexpr int pair_cy(int p) {
+  switch (p) {
+    case 0: return 0;  case 1: return 1;
+    case 2: return 1;  case 3: return -1;
+    case 4: return 0;  case 5: return 2;
+    case 6: return 1;  case 7: return -1; case 8: return 2;  case 9: return -2;
+    case 10: return 2; case 11: return -2;
+    case 12: return 0; case 13: return 3;
+    case 14: return 1; case 15: return -1; case 16: return 3; case 17: return -3;
+    default: return 0;
+  }
+}
+
+__host__ __device__ constexpr int pair_shell(int p) {
+  return p < 2 ? 1 : p < 4 ? 2 : p < 6 ? 3 : p < 10 ? 4 : p < 12 ? 5 : p < 14 ? 6 : 7;
+}
+
+__host__ __device__ constexpr int vel_cx(int l) { return l == 0 ? 0 : ((l - 1) % 2 == 0 ? 1 : -1) * pair_cx((l - 1) / 2); }
+__host__ __device__ constexpr int vel_cy(int l) { return l == 0 ? 0 : ((l - 1) % 2 == 0 ? 1 : -1) * pair_cy((l - 1) / 2); }
+__host__ __device__ constexpr int vel_shell(int l) { return l == 0 ? 0 : pair_shell((l - 1) / 2); }
+
+// |c|^2 of each shell.
+__host__ __device__ constexpr int shell_c2(int k) {
+  return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 4 : k == 4 ? 5 : k == 5 ? 8 : k == 6 ? 9 : 10;
+}
+
+// Host tables (used by the quadrature solve and the ABI).
+constexpr int kCx[kQ] = {vel_cx(0),  vel_cx(1),  vel_cx(2),  vel_cx(3),  vel_cx(4),  vel_cx(5),  vel_cx(6),
+                         vel_cx(7),  vel_cx(8),  vel_cx(9),  vel_cx(10), vel_cx(11), vel_cx(12), vel_cx(13),
+                         vel_cx(14), vel_cx(15), vel_cx(16), vel_cx(17), vel_cx(18), vel_cx(19), vel_cx(20),
+                         vel_cx(21), vel_cx(22), vel_cx(23), vel_cx(24), vel_cx(25), vel_cx(26), vel_cx(27),
+                         vel_cx(28), vel_cx(29), vel_cx(30), vel_cx(31), vel_cx(32), vel_cx(33), vel_cx(34),
+                         vel_cx(35), vel_cx(36)};
+constexpr int kCy[kQ] = {vel_cy(0),  vel_cy(1),  vel_cy(2),  vel_cy(3),  vel_cy(4),  vel_cy(5),  vel_cy(6),
+                         vel_cy(7),  vel_cy(8),  vel_cy(9),  vel_cy(10), vel_cy(11), vel_cy(12), vel_cy(13),
+                         vel_cy(14), vel_cy(15), vel_cy(16), vel_cy(17), vel_cy(18), vel_cy(19), vel_cy(20),
+                         vel_cy(21), vel_cy(22), vel_cy(23), vel_cy(24), vel_cy(25), vel_cy(26), vel_cy(27),
+                         vel_cy(28), vel_cy(29), vel_cy(30), vel_cy(31), vel_cy(32), vel_cy(33), vel_cy(34),
+                         vel_cy(35), vel_cy(36)};
+constexpr int kShellOf[kQ] = {
+    vel_shell(0),  vel_shell(1),  vel_shell(2),  vel_shell(3),  vel_shell(4),  vel_shell(5),  vel_shell(6),
+    vel_shell(7),  vel_shell(8),  vel_shell(9),  vel_shell(10), vel_shell(11), vel_shell(12), vel_shell(13),
+    vel_shell(14), vel_shell(15), vel_shell(16), vel_shell(17), vel_shell(18), vel_shell(19), vel_shell(20),
+    vel_shell(21), vel_shell(22), vel_shell(23), vel_shell(24), vel_shell(25), vel_shell(26), vel_shell(27),
+    vel_shell(28), vel_shell(29), vel_shell(30), vel_shell(31), vel_shell(32), vel_shell(33), vel_shell(34),
+    vel_shell(35), vel_shell(36)};
+
+// Solve the quadrature (quadrature_dd.cpp).  False if no root was found.
+bool solve_quadrature(double* s, double w_shell[kShells]);
+
+// Constants of the equilibrium that depend only on the quadrature.  With
+// a = xi.u, q = |u|^2, theta = T - 1 and x2 = |xi|^2 = s^2 |c|^2, the 4th-order
+// Hermite equilibrium (D = 2) is f^eq = w rho P with
+//   P = C0 + a C1 + a^2 C2 + a^3 / 6 + a^4 / 24,
+//   C0 = 1 - q/2 + q^2/8 + theta [ (x2-2)/2 + q (4-x2)/4 + theta (x2^2-8 x2+8)/8 ],
+//   C1 = 1 - q/2 + theta (x2-4)/2,
+//   C2 = 1/2 - q/4 + theta (x2-6)/4,
+// i.e. per shell: alpha = (x2-2)/2, beta = (4-x2)/4, gamma = (x2^2-8x2+8)/8,
+// delta = (x2-4)/2, eps = (x2-6)/4.
+struct ShellConsts {
+  double s;
+  double s2;
+  double w[kShells];
+  double alpha[kShells], beta[kShells], gamma[kShells], delta[kShells], eps[kShells];
+};
+
+// Per-lattice parameters of one step, passed by value to every kernel.
+struct StepParams {
+  int Lx, Ly;
+  int NY;          // column stride (doubles)
+  int periodic_y;
+  long long plane; // population plane stride (doubles) = (Lx + 2 kHx) * NY
+  double omega;    // 1 / tau
+  double one_minus_omega;
+  double uy_shift;    // tau g_y = -tau g0: u_bar = u + tau g (Eq. MASTERSHIFT3)
+  double theta_shift; // T_bar - 1 - T = -tau^2 g0^2 / D - 1
+  double fw[2][kQ];   // wall equilibria f^eq(1, 0, T_wall): [0] bottom, [1] top
+  double inv_denom[2];// 1 / sum of fw over the missing (row, population) pairs
+};
+
+// f^eq of one site into feq[37] (host or device).
+__host__ __device__ inline void equilibrium(const ShellConsts& c, double rho, double ux, double uy, double T,
+                                            double* feq) {
+  const double q = ux * ux + uy * uy;
+  const double th = T - 1.0;
+  const double A0 = 1.0 + q * (-0.5 + 0.125 * q);
+  const double B1 = 1.0 - 0.5 * q;
+  const double B2 = 0.5 - 0.25 * q;
+  const double sux = c.s * ux, suy = c.s * uy;
+  feq[0] = rho * c.w[0] * (A0 + th * (c.alpha[0] + q * c.beta[0] + th * c.gamma[0]));
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    const int k = pair_shell(p);
+    const double C0 = A0 + th * (c.alpha[k] + q * c.beta[k] + th * c.gamma[k]);
+    const double C1 = B1 + th * c.delta[k];
+    const double C2 = B2 + th * c.eps[k];
+    const double a = pair_cx(p) * sux + pair_cy(p) * suy;
+    const double b = a * a;
+    const double even = C0 + b * (C2 + b * (1.0 / 24.0));
+    const double odd = a * (C1 + b * (1.0 / 6.0));
+    const double W = rho * c.w[k];
+    feq[1 + 2 * p] = W * (even + odd);
+    feq[2 + 2 * p] = W * (even - odd);
+  }
+}
+
+}  // namespace d2q37

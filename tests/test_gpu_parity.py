@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the CPU
+oracle on the same seeded inputs.
+
+Bars (FP64):
+  * propagate (pbc + pull): bit-exact, it only moves values;
+  * propagate + bc, collide, initial state: per population plane,
+    max |a - b| / max |b| <= 1e-14.  The two sides evaluate the equilibrium in
+    different but equivalent forms; near T = 0.5 the 4th-order equilibrium of
+    some shells passes through zero, so an elementwise relative bar would
+    measure cancellation, not disagreement;
+  * full steps: per field ||a - b||_inf / ||b||_inf <= 1e-12 after 100 steps
+    (rho, u jointly over both components, T).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1703_00185_gb300 as lbm
+from tests import synthetic
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_00185_gb300 import _build
+    _build.build()
+    lbm.load_library()
+
+
+@pytest.fixture(scope="module")
+def perm():
+    """perm[l_library] = l_oracle, matched by velocity vector."""
+    cx, cy = lbm.lbm_velocity_set()
+    ocx, ocy = oracle.velocity_set()
+    idx = {(a, b): i for i, (a, b) in enumerate(zip(ocx.tolist(), ocy.tolist()))}
+    return np.array([idx[(a, b)] for a, b in zip(cx.tolist(), cy.tolist())])
+
+
+POP_TOL = 1e-14
+
+
+def plane_rel_err(a, b):
+    """max over populations l of max|a_l - b_l| / max|b_l| (arrays [37, ...])."""
+    a, b = a.reshape(37, -1), b.reshape(37, -1)
+    return float(np.max(np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)))
+
+
+def rel_field_errors(a, b):
+    return tuple(float(np.max(np.abs(x - y)) / np.max(np.abs(y))) for x, y in zip(a, b))
+
+
+def random_state(Lx, Ly, seed):
+    _, w = oracle.scale_and_weights()
+    return synthetic.random_populations(w, Lx, Ly, seed, rel_noise=0.1)  # oracle order
+
+
+def pair(Lx, Ly, kernel="separate", **kw):
+    return (lbm.Lattice(Lx, Ly, kernel=kernel, device="cuda:0", **kw), oracle.Lattice(Lx, Ly, **kw))
+
+
+SIZES = [(7, 10, False), (33, 130, False), (256, 128, False), (3, 6, False), (5, 6, True), (17, 40, True),
+         (130, 257, False)]
+
+
+@pytest.mark.parametrize("Lx,Ly,periodic_y", SIZES)
+def test_propagate_bit_exact(Lx, Ly, periodic_y, perm):
+    g, o = pair(Lx, Ly, periodic_y=periodic_y)
+    f = random_state(Lx, Ly, Lx * 1000 + Ly)
+    o.set_populations(f)
+    g.set_populations(f[perm])
+    for _ in range(3):
+        o.run(1, oracle.PHASE_PROPAGATE)
+        g.run_phases(1, lbm.PHASE_PROPAGATE)
+        assert np.array_equal(g.populations(), o.populations()[perm])
+
+
+@pytest.mark.parametrize("Lx,Ly,periodic_y", SIZES)
+def test_propagate_bc(Lx, Ly, periodic_y, perm):
+    g, o = pair(Lx, Ly, periodic_y=periodic_y, T_top=0.6, T_bot=1.4)
+    f = random_state(Lx, Ly, Lx + Ly)
+    o.set_populations(f)
+    g.set_populations(f[perm])
+    o.run(1, oracle.PHASE_PROPAGATE | oracle.PHASE_BC)
+    g.run_phases(1, lbm.PHASE_PROPAGATE | lbm.PHASE_BC)
+    a, b = g.populations(), o.populations()[perm]
+    assert plane_rel_err(a, b) <= POP_TOL
+
+
+@pytest.mark.parametrize("tau,g0", [(0.8, 1e-4), (0.6, 1e-3), (1.0, 0.0), (1.5, 1e-2)])
+def test_collide(tau, g0, perm):
+    Lx, Ly = 37, 45
+    g, o = pair(Lx, Ly, tau=tau, g0=g0)
+    rho, ux, uy, T = synthetic.random_fields(Lx, Ly, 11)
+    o.set_equilibrium(rho, ux, uy, T)
+    f = o.populations() * (1.0 + 0.02 * (2.0 * np.random.default_rng(3).random((37, Lx, Ly)) - 1.0))
+    o.set_populations(f)
+    g.set_populations(f[perm])
+    o.run(1, oracle.PHASE_COLLIDE)
+    g.run_phases(1, lbm.PHASE_COLLIDE)
+    a, b = g.populations(), o.populations()[perm]
+    assert plane_rel_err(a, b) <= POP_TOL
+
+
+def test_init_rayleigh_taylor_matches(perm):
+    g, o = pair(256, 128)
+    g.init_rayleigh_taylor(1)
+    o.init_rayleigh_taylor(1)
+    a, b = g.populations(), o.populations()[perm]
+    assert plane_rel_err(a, b) <= POP_TOL
+    errs = rel_field_errors(g.fields(), o.fields())
+    assert max(errs) < 1e-14, errs
+
+
+@pytest.fixture(scope="module")
+def c1_reference():
+    """256 x 128 Rayleigh-Taylor, seed 1, 100 steps on the oracle."""
+    o = oracle.Lattice(256, 128, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5)
+    o.init_rayleigh_taylor(1)
+    o.run(100)
+    return o.fields()
+
+
+@pytest.mark.parametrize("kernel", ["separate", "fused"])
+def test_full_step_256x128_100_steps(kernel, c1_reference):
+    g = lbm.Lattice(256, 128, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5, kernel=kernel, device="cuda:0")
+    g.init_rayleigh_taylor(1)
+    n0 = g.launch_count
+    g.step(100)
+    assert g.launch_count - n0 == (2 if kernel == "fused" else 4) * 100
+    errs = rel_field_errors(g.fields(), c1_reference)
+    assert max(errs) <= FIELD_TOL, errs
+
+
+def test_fused_equals_separate():
+    a = lbm.Lattice(256, 128, kernel="separate", device="cuda:0")
+    b = lbm.Lattice(256, 128, kernel="fused", device="cuda:0")
+    for x in (a, b):
+        x.init_rayleigh_taylor(4)
+        x.step(10)
+    fa, fb = a.populations(), b.populations()
+    assert plane_rel_err(fa, fb) <= 1e-15
+
+
+RANDOM_CASES = [tuple(v) for v in np.random.default_rng(2024).integers([3, 6], [41, 41], size=(6, 2))]
+
+
+@pytest.mark.parametrize("Lx,Ly", RANDOM_CASES)
+@pytest.mark.parametrize("kernel", ["separate", "fused"])
+def test_random_small_lattices(Lx, Ly, kernel, perm):
+    rng = np.random.default_rng(Lx * 100 + Ly)
+    tau = float(rng.choice([0.6, 1.0, 1.5]))
+    periodic_y = bool(rng.integers(2))
+    kw = dict(tau=tau, g0=1e-3, T_top=0.7, T_bot=1.3, periodic_y=periodic_y)
+    g, o = pair(int(Lx), int(Ly), kernel=kernel, **kw)
+    rho, ux, uy, T = synthetic.random_fields(int(Lx), int(Ly), 5)
+    o.set_equilibrium(rho, ux, uy, T)
+    g.set_populations(o.populations()[perm])
+    o.run(10)
+    g.step(10)
+    errs = rel_field_errors(g.fields(), o.fields())
+    assert max(errs) <= FIELD_TOL, errs
+
+
+def test_fields_device_matches_host():
+    import torch
+    g = lbm.Lattice(40, 24, device="cuda:0")
+    g.init_rayleigh_taylor(3)
+    g.step(5)
+    rho, u, T = g.fields()
+    dr, du, dT = (t.cpu().numpy() for t in g.fields_device())
+    torch.cuda.synchronize()
+    assert np.array_equal(rho, dr) and np.array_equal(u, du) and np.array_equal(T, dT)
+
+
+def test_errors_and_edge_cases():
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Lattice(2, 16, device="cuda:0")
+    with pytest.raises(lbm.LBMError):
+        lbm.Lattice(16, 5, device="cuda:0")
+    g = lbm.Lattice(16, 16, device="cuda:0")
+    with pytest.raises(lbm.LBMError) as e:
+        g.step(1)
+    assert e.value.code == lbm.LBM_ESTATE
+    g.init_rayleigh_taylor(1)
+    with pytest.raises(lbm.LBMError) as e:
+        g.run_phases(1, lbm.PHASE_BC)
+    assert e.value.code == lbm.LBM_EINVAL
+    before = g.populations()
+    g.step(0)
+    assert np.array_equal(g.populations(), before)
+    lbm.lbm_destroy(None)
+    # library-owned memory and stream
+    p = lbm.lbm_default_params()
+    h = lbm.lbm_create(32, 16, p)
+    lbm.lbm_init_rayleigh_taylor(h, 1)
+    lbm.lbm_step(h, 3)
+    lbm.lbm_synchronize(h)
+    assert lbm.lbm_launch_count(h) == 1 + 3 * 2
+    lbm.lbm_destroy(h)
+
+
+def test_full_size_sampled_columns(perm):
+    """2048 x 8192 in the fused schedule bench.py times: 2 steps from the
+    Rayleigh-Taylor state, sampled columns recomputed by the oracle on 13-column
+    windows (after 2 steps a column depends on its +-6 neighbours only), plus
+    global mass conservation."""
+    Lx, Ly, seed, steps = 2048, 8192, 1, 2
+    g = lbm.Lattice(Lx, Ly, kernel="fused", device="cuda:0")
+    g.init_rayleigh_taylor(seed)
+    m0 = g.fields()[0].sum()
+    g.step(steps)
+    f = g.populations()
+    m1 = g.fields()[0].sum()
+    assert abs(m1 - m0) / m0 < 1e-13
+    g.close()
+    T = oracle.rt_temperature(Lx, Ly, seed, 0.5, 1.5)
+    for x in (0, 1, 2, 777, 1024, 2045, 2047):
+        cols = [(x + d) % Lx for d in range(-6, 7)]
+        o = oracle.Lattice(13, Ly)
+        t = T[cols]
+        o.set_equilibrium(1.0 / t, 0.0, 0.0, t)
+        o.run(steps)
+        ref = o.populations()[perm][:, 6]
+        got = f[:, x]
+        assert plane_rel_err(got, ref) <= POP_TOL, x
