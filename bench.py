@@ -29,8 +29,11 @@ METRIC = "MLUPS per step"
 UNIT = "MLUPS"
 BYTES_PER_SITE = 592          # 37 FP64 populations read + 37 written per site update
 # FP64 flops the fused kernel executes per site: DADD + DMUL + 2 DFMA from the
-# ncu instruction counters of the fused kernel (89.15 + 107.06 + 2 x 209.00)
-FP64_FLOPS_PER_SITE = 614.2
+# ncu instruction counters of the fused kernel (17.15 + 106.06 + 2 x 178.00)
+FP64_FLOPS_PER_SITE = 479.2
+# DRAM bytes per fused launch at 2048 x 8192, scaled by sites from the ncu
+# capture of the same kernel on 2048 x 1024 (1259.4 MB per launch there)
+FUSED_TRAFFIC_BYTES_2048x8192 = 1259.4e6 * 8
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -183,7 +186,9 @@ def run_ours(a):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local_rank)
     sites = a.Lx * a.Ly
-    lat = lbm.Lattice(a.Lx, a.Ly, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5, kernel=a.kernel, device=dev)
+    stream = torch.cuda.Stream(device=dev)  # a capturable stream of the lattice's own
+    lat = lbm.Lattice(a.Lx, a.Ly, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5, kernel=a.kernel, device=dev,
+                      stream=stream)
     lat.init_rayleigh_taylor(1 + rank)
     for _ in range(a.warmup):
         lat.step(1)

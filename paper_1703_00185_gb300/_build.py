@@ -31,7 +31,7 @@ def _flags(src):
     common = ["-std=c++17", "-O3", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I" + os.path.join(HERE, "..", "include")]
     if not src.endswith(".cu"):
         return common + ["-x", "c++"]
-    flags = common + ARCH + ["-lineinfo"]
+    flags = common + ARCH + ["-lineinfo"] + os.environ.get("D2Q37_NVCC_FLAGS", "").split()
     if os.environ.get("D2Q37_PTXAS_V"):
         flags += ["-Xptxas", "-v"]
     return flags

@@ -24,7 +24,10 @@ struct lbm_t {
   cudaStream_t stream;
   bool owns_stream;
   bool have_state;
+  bool halo_valid;  // halo columns (and rows, if y is periodic) mirror the current state
   int64_t launches;
+  cudaGraphExec_t graph2[2];  // two fused steps starting from buffer 0 / 1
+  bool graph_unavailable;
   // per-kernel timing: event pairs recorded around launches, folded into the
   // totals when the stream is synchronised
   bool timing;
@@ -205,16 +208,19 @@ uint64_t splitmix64(uint64_t v) {
 }
 
 int step_once(lbm_t* h, int phases, bool fused) {
-  double* src = h->buf[h->cur];
-  double* dst = h->buf[1 - h->cur];
   int rc = LBM_OK;
   if (phases & LBM_PHASE_PROPAGATE) {
-    rc = run_kernel(h, LBM_KIND_WRAP, [&] { return launch_wrap(src, h->sp, h->stream); });
-    if (rc) return rc;
+    double* src = h->buf[h->cur];
+    double* dst = h->buf[1 - h->cur];
+    if (!h->halo_valid) {
+      rc = run_kernel(h, LBM_KIND_WRAP, [&] { return launch_wrap(src, h->sp, h->stream); });
+      if (rc) return rc;
+      h->halo_valid = true;
+    }
     if (fused) {
       rc = run_kernel(h, LBM_KIND_FUSED, [&] { return launch_fused(src, dst, h->sp, h->stream); });
       if (rc) return rc;
-      h->cur = 1 - h->cur;
+      h->cur = 1 - h->cur;  // fused writes the halo images of dst
       return LBM_OK;
     }
     rc = run_kernel(h, LBM_KIND_PROPAGATE, [&] { return launch_propagate(src, dst, h->sp, h->stream); });
@@ -224,10 +230,44 @@ int step_once(lbm_t* h, int phases, bool fused) {
       if (rc) return rc;
     }
     h->cur = 1 - h->cur;
+    h->halo_valid = false;  // propagate writes physical sites only
   }
-  if (phases & LBM_PHASE_COLLIDE)
+  if (phases & LBM_PHASE_COLLIDE) {
     rc = run_kernel(h, LBM_KIND_COLLIDE, [&] { return launch_collide(h->buf[h->cur], h->sp, h->stream); });
+    if (!rc) h->halo_valid = true;  // collide writes the halo images
+  }
   return rc;
+}
+
+// Two fused steps captured once per starting buffer and replayed: one graph
+// launch instead of two kernel launches.  Returns false (and the caller
+// launches directly) when the stream cannot be captured, e.g. the legacy
+// default stream.
+bool fused_pair_graph(lbm_t* h, cudaGraphExec_t* out) {
+  if (h->graph_unavailable) return false;
+  cudaGraphExec_t& g = h->graph2[h->cur];
+  if (!g) {
+    const int c = h->cur;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      h->graph_unavailable = true;
+      return false;
+    }
+    const int n1 = launch_fused(h->buf[c], h->buf[1 - c], h->sp, h->stream);
+    const int n2 = launch_fused(h->buf[1 - c], h->buf[c], h->sp, h->stream);
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (e != cudaSuccess || n1 < 0 || n2 < 0 || cudaGraphInstantiate(&g, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      g = nullptr;
+      h->graph_unavailable = true;
+      return false;
+    }
+    cudaGraphDestroy(graph);
+  }
+  *out = g;
+  return true;
 }
 
 }  // namespace
@@ -336,7 +376,10 @@ int lbm_init_rayleigh_taylor(lbm_t* h, uint64_t seed) {
     rc = run_kernel(h, LBM_KIND_INIT,
                     [&] { return launch_init_equilibrium(h->buf[h->cur], h->scratch, h->sp, h->stream); });
   if (!rc) rc = check(cudaStreamSynchronize(h->stream));
-  if (!rc) h->have_state = true;
+  if (!rc) {
+    h->have_state = true;
+    h->halo_valid = false;
+  }
   return rc;
 }
 
@@ -350,6 +393,7 @@ int lbm_set_populations(lbm_t* h, const double* f) {
     if (e != cudaSuccess) return LBM_ECUDA;
   }
   h->have_state = true;
+  h->halo_valid = false;
   return LBM_OK;
 }
 
@@ -370,7 +414,21 @@ int lbm_step(lbm_t* h, int n) {
   if (!h || n < 0) return LBM_EINVAL;
   if (!h->have_state) return LBM_ESTATE;
   const bool fused = h->prm.kernel == LBM_KERNEL_FUSED;
-  for (int t = 0; t < n; ++t) {
+  int t = 0;
+  if (fused && !h->timing && n >= 4) {
+    if (!h->halo_valid) {
+      const int rc = step_once(h, LBM_PHASE_ALL, true);
+      if (rc) return rc;
+      ++t;
+    }
+    cudaGraphExec_t g;
+    while (n - t >= 2 && fused_pair_graph(h, &g)) {
+      if (cudaGraphLaunch(g, h->stream) != cudaSuccess) return LBM_ECUDA;
+      h->launches += 2;
+      t += 2;  // two swaps: the current buffer is unchanged
+    }
+  }
+  for (; t < n; ++t) {
     const int rc = step_once(h, LBM_PHASE_ALL, fused);
     if (rc) return rc;
   }
@@ -442,6 +500,8 @@ void lbm_destroy(lbm_t* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   drain_timing(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  for (cudaGraphExec_t g : h->graph2)
+    if (g) cudaGraphExecDestroy(g);
   if (h->owns_stream && h->stream) cudaStreamDestroy(h->stream);
   if (h->owned) cudaFree(h->owned);
   delete h;

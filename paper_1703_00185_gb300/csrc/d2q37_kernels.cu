@@ -7,7 +7,10 @@
 // column starts on a 128-byte boundary.  Two frames are double-buffered.
 //
 // Kernels and the step sequence (Sec. "Code Organization"):
-//   wrap      pbc: fill the 3-column x halos (and y halos when y is periodic)
+//   wrap      pbc: fill the 3-column x halos (and y halos when y is periodic);
+//             needed only after a state is uploaded or after a propagate
+//             without collide, because collide and fused write the halo
+//             images of the edge columns themselves (store_site)
 //   propagate pull form of Eq. master2: dst_l(x,y) = src_l(x - c_lx, y - c_ly)
 //   bc        diffuse walls on rows 0..2 and Ly-3..Ly-1
 //   collide   BGK relaxation (Eq. discrete) to the shifted equilibrium of
@@ -30,16 +33,23 @@ namespace {
 
 constexpr int kBlockY = 128;
 
+// Minimum resident blocks per SM requested for the FP64 site kernels (caps
+// their registers at 65536 / (128 * blocks)); tuned on GB300.
+#ifndef D2Q37_SITE_MIN_BLOCKS
+#define D2Q37_SITE_MIN_BLOCKS 3
+#endif
+
 __device__ __forceinline__ long long site_index(const StepParams& p, int x, int y) {
-  return (long long)(x + kHx) * p.NY + (y + kHy);
+  return (long long)(x + kHx) * p.NY + (y + p.Hy);
 }
 
 // rho, u and T of one site (Sec. "Lattice Boltzmann methods"):
 // rho = sum f, rho u = s sum c f, D rho T = sum |xi|^2 f - rho |u|^2 (D = 2),
 // the last being sum |xi - u|^2 f expanded.  Pair sums and differences carry
-// the even and odd moments.
-__device__ __forceinline__ void site_moments(const double (&f)[kQ], double& rho, double& ux, double& uy,
-                                             double& T) {
+// the even and odd moments.  FP64 arithmetic throughout (reference form, and
+// the fallback of site_moments_fixed).
+__device__ __forceinline__ void site_moments_fp64(const double (&f)[kQ], double& rho, double& ux, double& uy,
+                                                  double& T) {
   double sh[kShells];
   sh[0] = f[0];
 #pragma unroll
@@ -66,6 +76,74 @@ __device__ __forceinline__ void site_moments(const double (&f)[kQ], double& rho,
   T = 0.5 * (c_shell.s2 * e * inv_rho - (ux * ux + uy * uy));
 }
 
+// The same moments with the sums done in 64-bit integers, off the FP64 pipe
+// (GB300 issues 2 FP64 operations per SM per clock but 64+ integer ones).
+// Every population is rounded to the grid of the site's largest exponent,
+// 2^(emax - 1075), i.e. to 53 bits relative to the largest population, and
+// summed exactly: rho and the moment sums carry one rounding per term at
+// that grid (comparable to an FP64 sum) and none from the additions.
+// Headroom: |term| < 2^53, |c|^2 <= 10 and 37 terms keep every sum < 2^62.
+// Sites with a population that is zero-exponent tiny (< 2^-960), infinite or
+// NaN take the FP64 form.
+__device__ __forceinline__ long long fixed_term(double v, int emax) {
+  const int hi = __double2hiint(v);
+  const unsigned lo = (unsigned)__double2loint(v);
+  const int e = (hi >> 20) & 0x7FF;
+  const long long mant = ((long long)((hi & 0xFFFFF) | (e ? 0x100000 : 0)) << 32) | lo;
+  const int sh = min(emax - max(e, 1), 62);
+  const long long r = sh ? (mant + (1LL << (sh - 1))) >> sh : mant;  // round half up
+  return hi < 0 ? -r : r;
+}
+
+__device__ __forceinline__ void site_moments(const double (&f)[kQ], double& rho, double& ux, double& uy,
+                                             double& T) {
+  int emax = 0;
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) emax = max(emax, (__double2hiint(f[l]) >> 20) & 0x7FF);
+  if (emax < 64 || emax > 2046) {
+    site_moments_fp64(f, rho, ux, uy, T);
+    return;
+  }
+  long long sh[kShells];
+  sh[0] = fixed_term(f[0], emax);
+#pragma unroll
+  for (int k = 1; k < kShells; ++k) sh[k] = 0;
+  long long jx = 0, jy = 0;
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    const long long vp = fixed_term(f[1 + 2 * p], emax);
+    const long long vm = fixed_term(f[2 + 2 * p], emax);
+    sh[pair_shell(p)] += vp + vm;
+    const long long d = vp - vm;
+    jx += pair_cx(p) * d;
+    jy += pair_cy(p) * d;
+  }
+  long long r = sh[0], e = 0;
+#pragma unroll
+  for (int k = 1; k < kShells; ++k) {
+    r += sh[k];
+    e += shell_c2(k) * sh[k];
+  }
+  const double rd = (double)r;
+  const double inv = 1.0 / rd;  // the grid scale cancels in u and T
+  ux = c_shell.s * (double)jx * inv;
+  uy = c_shell.s * (double)jy * inv;
+  T = 0.5 * (c_shell.s2 * (double)e * inv - (ux * ux + uy * uy));
+  rho = rd * __hiloint2double((emax - 52) << 20, 0);  // 2^(emax - 1075)
+}
+
+// c v for a hop component c in -3..3 given the multiples m = {v, 2v, 3v}.
+__device__ __forceinline__ double hop_term(int c, const double (&m)[3]) {
+  return c > 0 ? m[c - 1] : -m[-c - 1];
+}
+
+// cx ux + cy uy from precomputed multiples: one addition at most.
+__device__ __forceinline__ double hop_dot(int cx, int cy, const double (&mx)[3], const double (&my)[3]) {
+  if (cx == 0) return hop_term(cy, my);
+  if (cy == 0) return hop_term(cx, mx);
+  return hop_term(cx, mx) + hop_term(cy, my);
+}
+
 // BGK collision of one site, f <- f - (f - f^eq(rho, u_bar, T_bar)) / tau with
 // u_bar = u + tau g, T_bar = T - tau^2 g^2 / D (Eq. MASTERSHIFT3, Eq. discrete).
 // The equilibrium is evaluated per pair as even +- odd parts with per-shell
@@ -81,6 +159,9 @@ __device__ __forceinline__ void collide_site(double (&f)[kQ], const StepParams& 
   const double B1 = 1.0 - 0.5 * q;
   const double B2 = 0.5 - 0.25 * q;
   const double sux = c_shell.s * ubx, suy = c_shell.s * uby;
+  // a = xi.u_bar = cx sux + cy suy with |cx|, |cy| <= 3: multiples formed once
+  const double mx[3] = {sux, sux + sux, sux + sux + sux};
+  const double my[3] = {suy, suy + suy, suy + suy + suy};
   const double wr = p.omega * rho;
   const double keep = p.one_minus_omega;
   {
@@ -98,7 +179,7 @@ __device__ __forceinline__ void collide_site(double (&f)[kQ], const StepParams& 
 #pragma unroll
     for (int pr = 0; pr < kPairs; ++pr) {
       if (pair_shell(pr) != k) continue;
-      const double a = (double)pair_cx(pr) * sux + (double)pair_cy(pr) * suy;
+      const double a = hop_dot(pair_cx(pr), pair_cy(pr), mx, my);
       const double b = a * a;
       const double even = P0 + b * (P2 + b * P4);
       const double odd = a * (P1 + b * P3);
@@ -128,6 +209,29 @@ __device__ __forceinline__ double wall_density(const double* __restrict__ src, c
     }
   }
   return out * p.inv_denom[wall];
+}
+
+// Write the populations of physical site (x, y) and, for sites within 3 of a
+// periodic edge, their halo images, so the next pull finds the halos filled
+// (the pbc step folded into the writer; the halo columns see the same values
+// the wrap kernel would copy).  x is uniform across a block, so the extra
+// stores are divergence-free except on periodic y edges.
+__device__ __forceinline__ void store_site(double* __restrict__ dst, const StepParams& p, int x, int y,
+                                           const double (&f)[kQ]) {
+  int xs[3] = {x, 0, 0}, ys[3] = {y, 0, 0};
+  int nx = 1, ny = 1;
+  if (x < kHx) xs[nx++] = x + p.Lx;
+  if (x >= p.Lx - kHx) xs[nx++] = x - p.Lx;
+  if (p.periodic_y) {
+    if (y < kHx) ys[ny++] = y + p.Ly;
+    if (y >= p.Ly - kHx) ys[ny++] = y - p.Ly;
+  }
+  for (int a = 0; a < nx; ++a)
+    for (int b = 0; b < ny; ++b) {
+      const long long i = site_index(p, xs[a], ys[b]);
+#pragma unroll
+      for (int l = 0; l < kQ; ++l) dst[l * p.plane + i] = f[l];
+    }
 }
 
 __global__ void __launch_bounds__(256) wrap_kernel(double* __restrict__ buf, StepParams p) {
@@ -188,7 +292,7 @@ __global__ void __launch_bounds__(128) bc_kernel(const double* __restrict__ src,
   }
 }
 
-__global__ void __launch_bounds__(kBlockY) collide_kernel(double* __restrict__ buf, StepParams p) {
+__global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) collide_kernel(double* __restrict__ buf, StepParams p) {
   const int x = blockIdx.x;
   const int y = blockIdx.y * kBlockY + threadIdx.x;
   if (y >= p.Ly) return;
@@ -197,11 +301,10 @@ __global__ void __launch_bounds__(kBlockY) collide_kernel(double* __restrict__ b
 #pragma unroll
   for (int l = 0; l < kQ; ++l) f[l] = buf[l * p.plane + i];
   collide_site(f, p);
-#pragma unroll
-  for (int l = 0; l < kQ; ++l) buf[l * p.plane + i] = f[l];
+  store_site(buf, p, x, y, f);
 }
 
-__global__ void __launch_bounds__(kBlockY) fused_kernel(const double* __restrict__ src, double* __restrict__ dst,
+__global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(const double* __restrict__ src, double* __restrict__ dst,
                                                         StepParams p) {
   const int x = blockIdx.x;
   const int y = blockIdx.y * kBlockY + threadIdx.x;
@@ -221,8 +324,7 @@ __global__ void __launch_bounds__(kBlockY) fused_kernel(const double* __restrict
     }
   }
   collide_site(f, p);
-#pragma unroll
-  for (int l = 0; l < kQ; ++l) dst[l * p.plane + i] = f[l];
+  store_site(dst, p, x, y, f);
 }
 
 __global__ void __launch_bounds__(kBlockY) fields_kernel(const double* __restrict__ buf, double* __restrict__ rho,
@@ -256,6 +358,20 @@ __global__ void __launch_bounds__(kBlockY) init_equilibrium_kernel(double* __res
   const long long i = site_index(p, x, y);
 #pragma unroll
   for (int l = 0; l < kQ; ++l) buf[l * p.plane + i] = feq[l];
+}
+
+// The same initial state stored as FP32 deviations d_l = f_l - w_l.
+__global__ void __launch_bounds__(kBlockY) init_equilibrium32_kernel(float* __restrict__ buf,
+                                                                     const double* __restrict__ T, StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  const double t = T[(long long)x * p.Ly + y];
+  double feq[kQ];
+  equilibrium(c_shell, 1.0 / t, 0.0, 0.0, t, feq);
+  const long long i = site_index(p, x, y);
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) buf[l * p.plane + i] = (float)(feq[l] - c_shell.w[vel_shell(l)]);
 }
 
 dim3 site_grid(const StepParams& p) { return dim3(p.Lx, (p.Ly + kBlockY - 1) / kBlockY); }
@@ -302,6 +418,11 @@ int launch_fields(const double* buf, double* rho, double* u, double* T, const St
 
 int launch_init_equilibrium(double* buf, const double* T, const StepParams& p, cudaStream_t stream) {
   init_equilibrium_kernel<<<site_grid(p), kBlockY, 0, stream>>>(buf, T, p);
+  return done(1);
+}
+
+int launch_init_equilibrium32(float* buf, const double* T, const StepParams& p, cudaStream_t stream) {
+  init_equilibrium32_kernel<<<site_grid(p), kBlockY, 0, stream>>>(buf, T, p);
   return done(1);
 }
 

@@ -99,12 +99,32 @@ struct ShellConsts {
   double alpha[kShells], beta[kShells], gamma[kShells], delta[kShells], eps[kShells];
 };
 
+// FP32 deviation storage: populations are stored as d_l = f_l - w_l in FP32,
+// with 32 halo rows (128 bytes) above and below.
+constexpr int kHy32 = 32;
+
+// Quadrature constants for the FP32-storage kernels: the wide-precision ones
+// as FP64 and as double-float (hi, lo) pairs, the rest in FP32.
+struct ShellConsts32 {
+  double s, s2;
+  float s_hi, s_lo, s2_hi, s2_lo;
+  double x2[kShells];  // s^2 |c|^2 per shell
+  float x2_hi[kShells], x2_lo[kShells];
+  double w64[kShells];
+  float w[kShells];
+  float delta[kShells], eps[kShells];  // (x2 - 4)/2, (x2 - 6)/4
+};
+
 // Per-lattice parameters of one step, passed by value to every kernel.
 struct StepParams {
   int Lx, Ly;
-  int NY;          // column stride (doubles)
+  int NY;          // column stride (elements)
+  int Hy;          // halo rows below the lattice (16 for FP64, 32 for FP32 storage)
   int periodic_y;
-  long long plane; // population plane stride (doubles) = (Lx + 2 kHx) * NY
+  long long plane; // population plane stride (elements) = (Lx + 2 kHx) * NY
+  float omega_f, keep_f;  // 1/tau and 1 - 1/tau rounded to FP32 (FP32 storage)
+  float uy_shift_df[2];    // uy_shift and theta_shift as double-float (hi, lo) pairs
+  float theta_shift_df[2];
   double omega;    // 1 / tau
   double one_minus_omega;
   double uy_shift;    // tau g_y = -tau g0: u_bar = u + tau g (Eq. MASTERSHIFT3)

@@ -20,4 +20,15 @@ int launch_fused(const double* src, double* dst, const StepParams& p, cudaStream
 int launch_fields(const double* buf, double* rho, double* u, double* T, const StepParams& p, cudaStream_t stream);
 int launch_init_equilibrium(double* buf, const double* T, const StepParams& p, cudaStream_t stream);
 
+// FP32 deviation storage (d2q37_kernels_fp32.cu; init in d2q37_kernels.cu).
+// wide_fp64 selects FP64 (true) or double-float (false) for the wide terms.
+cudaError_t upload_shell_consts32(const ShellConsts32& c);
+int launch_wrap32(float* buf, const StepParams& p, cudaStream_t stream);
+int launch_propagate32(const float* src, float* dst, const StepParams& p, cudaStream_t stream);
+int launch_bc32(const float* src, float* dst, const StepParams& p, cudaStream_t stream);
+int launch_collide32(float* buf, const StepParams& p, bool wide_fp64, cudaStream_t stream);
+int launch_fused32(const float* src, float* dst, const StepParams& p, bool wide_fp64, cudaStream_t stream);
+int launch_fields32(const float* buf, double* rho, double* u, double* T, const StepParams& p, cudaStream_t stream);
+int launch_init_equilibrium32(float* buf, const double* T, const StepParams& p, cudaStream_t stream);
+
 }  // namespace d2q37
