@@ -22,12 +22,15 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS per step"
 UNIT = "MLUPS"
-BYTES_PER_SITE = 592          # 37 FP64 populations read + 37 written per site update
+# algorithmic bytes per site update: 37 populations read + 37 written
+BYTES_PER_SITE = {"fp64": 592, "fp32": 296, "fp32-df": 296}
 # FP64 flops the fused kernel executes per site: DADD + DMUL + 2 DFMA from the
 # ncu instruction counters of the fused kernel (17.15 + 106.06 + 2 x 178.00)
 FP64_FLOPS_PER_SITE = 479.2
@@ -45,6 +48,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--kernel", choices=["fused", "separate"], default="fused")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp32-df"], default="fp64")
+    ap.add_argument("--no-precision-forms", dest="precision_forms", action="store_false",
+                    help="skip timing the FP32-storage forms after the FP64 step")
+    ap.add_argument("--accuracy-steps", type=int, default=100,
+                    help="steps after which the FP32-storage forms are compared with the FP64 step")
     ap.add_argument("--Lx", type=int, default=2048)
     ap.add_argument("--Ly", type=int, default=8192)
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -172,6 +180,68 @@ def run_reference(a):
 
 # -------------------------------------------------------------------- GPU arm
 
+DTYPES = {"fp64": "f64", "fp32": "f32 storage + f64 wide terms", "fp32-df": "f32 storage + double-float wide terms"}
+
+
+def roofline_of(kind, avg_s, sites, precision, traffic=None):
+    """Roofline entry of the dominant kernel: FP64-pipe bound for the FP64 form,
+    HBM bound for the FP32-storage forms."""
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    nbytes = (BYTES_PER_SITE[precision] if kind in ("fused", "propagate", "collide") else 0) * sites
+    hbm = {"algorithmic_bytes_per_launch": nbytes, "achieved_gbs": round(nbytes / avg_s / 1e9, 1),
+           "peak_gbs": hbm_peak, "frac": round(nbytes / avg_s / 1e9 / hbm_peak, 4) if hbm_peak else None,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    if precision == "fp64":
+        r = {"bound": "alu", "kernel": kind, "achieved": None, "peak": round(FP64_PEAK_TFLOPS, 4),
+             "unit": "TFLOP/s", "frac": None, "traffic": traffic,
+             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
+        if kind in ("fused", "collide"):
+            achieved = FP64_FLOPS_PER_SITE * sites / avg_s / 1e12
+            r.update(achieved=round(achieved, 4), frac=round(achieved / FP64_PEAK_TFLOPS, 4))
+        r["hbm"] = hbm
+    else:
+        r = {"bound": "hbm", "kernel": kind, "achieved": hbm["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+             "frac": hbm["frac"], "traffic": traffic, "peak_source": hbm["peak_source"]}
+    r["avg_launch_ms"] = round(avg_s * 1e3, 4)
+    return r
+
+
+def time_form(torch, lbm, a, dev, precision, kernel, steps, seed, dist=None, sampler=None):
+    """Advance one lattice `steps` steps between CUDA events on its stream; per
+    kernel event pairs from the library give the dominant kernel's launch time."""
+    stream = torch.cuda.Stream(device=dev)  # a capturable stream of the lattice's own
+    lat = lbm.Lattice(a.Lx, a.Ly, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5, kernel=kernel, device=dev,
+                      stream=stream, precision=precision)
+    lat.init_rayleigh_taylor(seed)
+    for _ in range(a.warmup):
+        lat.step(1)
+    lat.synchronize()
+    lat.set_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)  # let nvidia-smi take its first samples
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = lat.launch_count
+    e0.record(lat.stream)
+    for _ in range(steps):
+        lat.step(1)
+    e1.record(lat.stream)
+    e1.synchronize()
+    torch.cuda.synchronize(dev)
+    launches = lat.launch_count - n0
+    ms = e0.elapsed_time(e1)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    kt = lat.kernel_times()
+    lat.set_timing(False)
+    return lat, ms, launches, kt, clocks
+
+
 def run_ours(a):
     rank, local_rank, world = dist_env()
     cpu = None
@@ -186,62 +256,20 @@ def run_ours(a):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local_rank)
     sites = a.Lx * a.Ly
-    stream = torch.cuda.Stream(device=dev)  # a capturable stream of the lattice's own
-    lat = lbm.Lattice(a.Lx, a.Ly, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5, kernel=a.kernel, device=dev,
-                      stream=stream)
-    lat.init_rayleigh_taylor(1 + rank)
-    for _ in range(a.warmup):
-        lat.step(1)
-    lat.synchronize()
     uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
     sampler = ClockSampler("GPU-" + str(uuid) if uuid is not None else None)
-    lat.set_timing(True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    sampler.start()
-    time.sleep(0.3)  # let nvidia-smi take its first samples
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n0 = lat.launch_count
-    e0.record(lat.stream)
-    for _ in range(a.steps):
-        lat.step(1)
-    e1.record(lat.stream)
-    e1.synchronize()
-    torch.cuda.synchronize(dev)
-    launches = lat.launch_count - n0
-    ms = e0.elapsed_time(e1)
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    kt = lat.kernel_times()
-    lat.set_timing(False)
+    lat, ms, launches, kt, clocks = time_form(torch, lbm, a, dev, a.precision, a.kernel, a.steps, 1 + rank,
+                                              dist, sampler)
     if dist:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     ms_per_step = ms / a.steps
     value = sites * world * a.steps / (ms * 1e-3) / 1e6
-
-    # dominant kernel of the timed region, its average launch from events on the launching stream
     kind = max(kt, key=lambda k: kt[k][0])
-    kms, kn = kt[kind]
-    avg_s = kms / kn * 1e-3
-    peaks = measured_peaks()
-    hbm_peak = peaks.get("hbm_gbs")
-    site_launch = sites
-    roofline = {"bound": "alu", "kernel": kind, "achieved": None, "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
-    if kind in ("fused", "collide"):
-        achieved = FP64_FLOPS_PER_SITE * site_launch / avg_s / 1e12
-        roofline.update(achieved=round(achieved, 4), frac=round(achieved / FP64_PEAK_TFLOPS, 4))
-    hbm_bytes = (BYTES_PER_SITE if kind in ("fused", "propagate", "collide") else 0) * site_launch
-    roofline["hbm"] = {"algorithmic_bytes_per_launch": hbm_bytes,
-                       "achieved_gbs": round(hbm_bytes / avg_s / 1e9, 1),
-                       "peak_gbs": hbm_peak, "frac": round(hbm_bytes / avg_s / 1e9 / hbm_peak, 4) if hbm_peak else None,
-                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    roofline["avg_launch_ms"] = round(avg_s * 1e3, 4)
+    traffic = FUSED_TRAFFIC_BYTES_2048x8192 if (kind == "fused" and a.precision == "fp64" and
+                                                 (a.Lx, a.Ly) == (2048, 8192)) else None
+    roofline = roofline_of(kind, kt[kind][0] / kt[kind][1] * 1e-3, sites, a.precision, traffic)
 
     # end to end through the C ABI with pinned host buffers: upload state, one step, read fields
     e2e = None
@@ -263,17 +291,44 @@ def run_ours(a):
                "d2h_bytes_per_step": (rho.numel() + u.numel() + T.numel()) * 8,
                "steps": a.e2e_steps}
     lat.close()
+
+    # the FP32-storage forms on the same workload, each against the FP64 step's fields
+    forms = {}
+    if a.precision_forms and a.precision == "fp64":
+        ref = lbm.Lattice(a.Lx, a.Ly, device=dev)
+        ref.init_rayleigh_taylor(1 + rank)
+        ref.step(a.accuracy_steps)
+        ref_fields = ref.fields()
+        ref.close()
+        for prec in ("fp32", "fp32-df"):
+            flat, fms, fl, fkt, _ = time_form(torch, lbm, a, dev, prec, "fused", a.steps, 1 + rank)
+            flat.close()
+            fkind = max(fkt, key=lambda k: fkt[k][0])
+            acc = lbm.Lattice(a.Lx, a.Ly, device=dev, precision=prec)
+            acc.init_rayleigh_taylor(1 + rank)
+            acc.step(a.accuracy_steps)
+            fields = acc.fields()
+            acc.close()
+            errs = [float(np.linalg.norm(x - y) / np.linalg.norm(y)) for x, y in zip(fields, ref_fields)]
+            forms[prec] = {"value": round(sites * a.steps / (fms * 1e-3) / 1e6, 3), "unit": UNIT,
+                           "ms_per_step": round(fms / a.steps, 4), "dtype": DTYPES[prec],
+                           "roofline": roofline_of(fkind, fkt[fkind][0] / fkt[fkind][1] * 1e-3, sites, prec),
+                           "rel_l2_vs_fp64_after_%d_steps" % a.accuracy_steps:
+                               {"rho": errs[0], "u": errs[1], "T": errs[2]},
+                           "gpu_launches": fl}
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[a.precision], "data": "synthetic",
                 "config": {"workload": workload_name(a), "Lx": a.Lx, "Ly": a.Ly, "kernel": a.kernel,
-                           "tau": 0.8, "g0": 1e-4, "T_top": 0.5, "T_bot": 1.5, "seed": "1 + rank",
+                           "precision": a.precision, "tau": 0.8, "g0": 1e-4, "T_top": 0.5, "T_bot": 1.5,
+                           "seed": "1 + rank",
                            "l2": "no flush: inputs exceed L2 (2 x %.2f GB population copies vs 129 MB)" %
-                                 (37 * (a.Lx + 6) * (a.Ly + 32) * 8 / 1e9),
+                                 (37 * (a.Lx + 6) * (a.Ly + 32) * (8 if a.precision == "fp64" else 4) / 1e9),
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "kernel_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]}, "clocks": clocks}
+                "kernel_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]}, "clocks": clocks,
+                "precision_forms": forms or None}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -49,6 +49,11 @@ extern "C" {
 #define LBM_PHASE_COLLIDE 4   /* BGK collide (Eq. discrete) */
 #define LBM_PHASE_ALL 7
 
+/* Storage precisions for lbm_params.precision. */
+#define LBM_PRECISION_FP64 0      /* FP64 populations, FP64 arithmetic */
+#define LBM_PRECISION_FP32_FP64 1 /* FP32 deviations f - w; FP64 for rho, u, T and T-dependent terms */
+#define LBM_PRECISION_FP32_DF 2   /* FP32 deviations; those terms in double-float on the FP32 pipes */
+
 /* Kernel schedules for lbm_params.kernel. */
 #define LBM_KERNEL_SEPARATE 0 /* pbc, propagate, bc, collide as separate kernels */
 #define LBM_KERNEL_FUSED 1    /* pbc, then one fused propagate+bc+collide kernel */
@@ -60,7 +65,10 @@ typedef struct {
   double g0;      /* gravity magnitude; g = (0, -g0) */
   double T_top;   /* top wall temperature */
   double T_bot;   /* bottom wall temperature */
-  int precision;  /* 0 = FP64 populations (the only value accepted by this version) */
+  int precision;  /* LBM_PRECISION_*: populations stored as FP64, or as FP32 deviations
+                     d_l = f_l - w_l from the lattice weights (half the memory traffic) with the
+                     moment sums exact in 64-bit integers and rho, u, T and the temperature-
+                     dependent equilibrium terms in FP64 or in double-float */
   int kernel;     /* LBM_KERNEL_SEPARATE or LBM_KERNEL_FUSED */
   int periodic_y; /* 1: no walls, y periodic too (used by tests of pure propagation) */
 } lbm_params;
@@ -77,9 +85,10 @@ int lbm_velocity_set(int* cx, int* cy);
  * solved by this library at first use.  Host only. */
 int lbm_quadrature(double* s, double* w);
 
-/* Device bytes needed for an Lx x Ly lattice: two FP64 population copies
- * of 37 x (Lx+6) x NY sites (NY = Ly + 32 rounded up to a multiple of 16)
- * plus field scratch.  0 for invalid sizes. */
+/* Device bytes needed for an Lx x Ly lattice: two population copies of
+ * 37 x (Lx+6) x NY sites (FP64: NY = Ly + 32 rounded up to 16; FP32
+ * storage: NY = Ly + 64 rounded up to 32) plus a scratch of 4 Lx Ly
+ * doubles.  0 for invalid sizes or parameters. */
 size_t lbm_required_bytes(int Lx, int Ly, const lbm_params* p);
 
 /* Create a lattice on the current CUDA device; allocates its own device
@@ -140,7 +149,8 @@ int64_t lbm_launch_count(const lbm_t* h);
 #define LBM_KIND_FUSED 4
 #define LBM_KIND_FIELDS 5
 #define LBM_KIND_INIT 6
-#define LBM_KIND_COUNT 7
+#define LBM_KIND_CONVERT 7 /* FP64 <-> FP32-deviation conversions of set/get populations */
+#define LBM_KIND_COUNT 8
 
 /* Per-kernel timing (not in the paper; measurement support).  enable != 0
  * records a CUDA event pair on the handle's stream around every later kernel
@@ -154,6 +164,44 @@ int lbm_kernel_times(lbm_t* h, double* ms, int64_t* launches);
 
 /* Release the handle and the device memory it allocated.  NULL-safe. */
 void lbm_destroy(lbm_t* h);
+
+/* ---- batched stepping: many lattices, one launch per step -----------------
+ * Not in the paper (its lattices are split across GPUs instead); this is the
+ * single-GPU form for many independent jobs.  Every lattice keeps its own
+ * memory, parameters and state (its lbm_t); the batch advances all of them by
+ * one step per launch of a grid-stride fused kernel over tiles (one column by
+ * block_y rows) of every lattice, and lbm_batch_step(n >= 4) replays a
+ * captured two-step CUDA graph.  Per-site arithmetic is the fused kernel's,
+ * so a lattice's result is the same batched or alone. */
+typedef struct lbm_batch_t lbm_batch_t;
+
+/* Group n lattices (same precision, each with a state) on cuda_stream (NULL:
+ * legacy default stream).  Synchronises the lattices' own streams.  The
+ * lattices must outlive the batch and must not be stepped through their own
+ * handles while the batch is in use; call lbm_batch_synchronize() before
+ * reading their fields or populations. */
+int lbm_batch_create(int n, lbm_t* const* lattices, void* cuda_stream, lbm_batch_t** out);
+
+/* n steps of every lattice, asynchronous on the batch stream. */
+int lbm_batch_step(lbm_batch_t* b, int n);
+
+/* Launch shape: block_y in {64, 128, 256} rows per tile; blocks_per_sm 0 for
+ * one block per tile, else a persistent grid of blocks_per_sm x SM count
+ * (at most the kernel's occupancy; LBM_EINVAL otherwise). */
+int lbm_batch_set_config(lbm_batch_t* b, int block_y, int blocks_per_sm);
+int lbm_batch_get_config(const lbm_batch_t* b, int* block_y, int* blocks_per_sm);
+
+/* Time every launch shape over trial_steps launches and keep the fastest;
+ * the trials recompute the same step, so the lattices' state does not
+ * advance.  Outputs (any may be NULL): the chosen shape and its ms per step.
+ * Synchronises the batch stream. */
+int lbm_batch_autotune(lbm_batch_t* b, int trial_steps, int* block_y, int* blocks_per_sm, double* best_ms);
+
+int lbm_batch_synchronize(lbm_batch_t* b);
+int64_t lbm_batch_launch_count(const lbm_batch_t* b);
+
+/* Release the batch (not its lattices).  NULL-safe. */
+void lbm_batch_destroy(lbm_batch_t* b);
 
 const char* lbm_strerror(int code);
 

@@ -17,6 +17,8 @@ Q = 37
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5
 PHASE_PROPAGATE, PHASE_BC, PHASE_COLLIDE, PHASE_ALL = 1, 2, 4, 7
 KERNEL_SEPARATE, KERNEL_FUSED = 0, 1
+PRECISION_FP64, PRECISION_FP32_FP64, PRECISION_FP32_DF = 0, 1, 2
+PRECISIONS = {"fp64": PRECISION_FP64, "fp32": PRECISION_FP32_FP64, "fp32-df": PRECISION_FP32_DF}
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libd2q37_gb300.so")
 
@@ -66,6 +68,14 @@ def load_library():
         "lbm_launch_count": (ctypes.c_int64, [vp]),
         "lbm_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_kernel_times": (ctypes.c_int, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
+        "lbm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp), vp, ctypes.POINTER(vp)]),
+        "lbm_batch_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_batch_set_config": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+        "lbm_batch_get_config": (ctypes.c_int, [vp, ip, ip]),
+        "lbm_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, dp]),
+        "lbm_batch_synchronize": (ctypes.c_int, [vp]),
+        "lbm_batch_launch_count": (ctypes.c_int64, [vp]),
+        "lbm_batch_destroy": (None, [vp]),
         "lbm_destroy": (None, [vp]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     }
@@ -82,10 +92,12 @@ def exported_symbols():
     return ["lbm_default_params", "lbm_velocity_set", "lbm_quadrature", "lbm_required_bytes", "lbm_create",
             "lbm_create_ext", "lbm_init_rayleigh_taylor", "lbm_set_populations", "lbm_get_populations",
             "lbm_step", "lbm_run_phases", "lbm_fields", "lbm_fields_device", "lbm_synchronize",
-            "lbm_launch_count", "lbm_set_timing", "lbm_kernel_times", "lbm_destroy", "lbm_strerror"]
+            "lbm_launch_count", "lbm_set_timing", "lbm_kernel_times", "lbm_destroy", "lbm_strerror",
+            "lbm_batch_create", "lbm_batch_step", "lbm_batch_set_config", "lbm_batch_get_config",
+            "lbm_batch_autotune", "lbm_batch_synchronize", "lbm_batch_launch_count", "lbm_batch_destroy"]
 
 
-KERNEL_KINDS = ("wrap", "propagate", "bc", "collide", "fused", "fields", "init")
+KERNEL_KINDS = ("wrap", "propagate", "bc", "collide", "fused", "fields", "init", "convert")
 
 
 def _check(rc, what):
@@ -198,12 +210,14 @@ def lbm_destroy(h):
 class Lattice:
     """One Lx x Ly lattice on a CUDA device, memory owned by PyTorch.
 
-    ``kernel`` is "fused" (pbc + one propagate/bc/collide kernel per step) or
-    "separate" (pbc, propagate, bc, collide).  All work runs on ``stream``
-    (default: the current PyTorch stream of ``device``)."""
+    ``kernel`` is "fused" (one propagate/bc/collide kernel per step) or
+    "separate" (propagate, bc, collide).  ``precision`` is "fp64", "fp32"
+    (FP32 deviation storage, FP64 wide terms) or "fp32-df" (FP32 deviation
+    storage, double-float wide terms).  All work runs on ``stream`` (default:
+    the current PyTorch stream of ``device``)."""
 
     def __init__(self, Lx, Ly, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5, kernel="fused", periodic_y=False,
-                 device=None, stream=None):
+                 device=None, stream=None, precision="fp64"):
         import torch
         self._torch = torch
         load_library()
@@ -214,6 +228,8 @@ class Lattice:
         p = lbm_default_params()
         p.tau, p.g0, p.T_top, p.T_bot = tau, g0, T_top, T_bot
         p.kernel = {"fused": KERNEL_FUSED, "separate": KERNEL_SEPARATE}[kernel]
+        p.precision = PRECISIONS[precision]
+        self.precision = precision
         p.periodic_y = int(bool(periodic_y))
         self.params = p
         nbytes = lbm_required_bytes(self.Lx, self.Ly, p)
@@ -301,3 +317,112 @@ class Lattice:
     def kernel_times(self):
         with self._dev():
             return lbm_kernel_times(self._h)
+
+
+# ------------------------------------------------------------------ Batch
+
+def _autotune_cache_path():
+    return os.environ.get("D2Q37_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "d2q37_gb300", "autotune.json"))
+
+
+class Batch:
+    """Many lattices advanced together, one launch of the batched fused kernel
+    per step (``lbm_batch_*``).  All lattices must share the precision and
+    have a state; while a batch is in use, step them only through it and call
+    :meth:`synchronize` before reading their fields."""
+
+    def __init__(self, lattices, stream=None):
+        import torch
+        self._torch = torch
+        lib = load_library()
+        if not lattices:
+            raise ValueError("empty batch")
+        self.lattices = list(lattices)
+        self.device = self.lattices[0].device
+        for lat in self.lattices:
+            lat.synchronize()
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+            arr = (ctypes.c_void_p * len(self.lattices))(*[lat._h.value for lat in self.lattices])
+            h = ctypes.c_void_p()
+            _check(lib.lbm_batch_create(len(self.lattices), arr, self.stream.cuda_stream, ctypes.byref(h)),
+                   "lbm_batch_create")
+            self._h = h
+
+    def _dev(self):
+        return self._torch.cuda.device(self.device)
+
+    def step(self, n=1):
+        with self._dev():
+            _check(load_library().lbm_batch_step(self._h, n), "lbm_batch_step")
+
+    def set_config(self, block_y, blocks_per_sm):
+        _check(load_library().lbm_batch_set_config(self._h, block_y, blocks_per_sm), "lbm_batch_set_config")
+
+    def config(self):
+        by, bps = ctypes.c_int(), ctypes.c_int()
+        _check(load_library().lbm_batch_get_config(self._h, ctypes.byref(by), ctypes.byref(bps)),
+               "lbm_batch_get_config")
+        return by.value, bps.value
+
+    def cache_key(self):
+        name = self._torch.cuda.get_device_name(self.device)
+        sites = sum(l.Lx * l.Ly for l in self.lattices)
+        return "%s|%s|n=%d|sites~2^%d" % (name, self.lattices[0].precision, len(self.lattices),
+                                           max(0, sites.bit_length() - 1))
+
+    def autotune(self, trial_steps=3, use_cache=True):
+        """Pick the fastest launch shape (does not advance the lattices).
+        With ``use_cache`` the choice is kept in a JSON file keyed by GPU,
+        precision, lattice count and total size, and reused."""
+        import json
+        path, key = _autotune_cache_path(), self.cache_key()
+        cache = {}
+        if use_cache and os.path.exists(path):
+            try:
+                with open(path) as fh:
+                    cache = json.load(fh)
+            except (OSError, ValueError):
+                cache = {}
+        if use_cache and key in cache:
+            by, bps = cache[key]["block_y"], cache[key]["blocks_per_sm"]
+            self.set_config(by, bps)
+            return {"block_y": by, "blocks_per_sm": bps, "ms_per_step": cache[key].get("ms_per_step"),
+                    "cached": True}
+        by, bps, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        with self._dev():
+            _check(load_library().lbm_batch_autotune(self._h, trial_steps, ctypes.byref(by), ctypes.byref(bps),
+                                                     ctypes.byref(ms)), "lbm_batch_autotune")
+        res = {"block_y": by.value, "blocks_per_sm": bps.value, "ms_per_step": ms.value, "cached": False}
+        if use_cache:
+            cache[key] = {k: res[k] for k in ("block_y", "blocks_per_sm", "ms_per_step")}
+            try:
+                os.makedirs(os.path.dirname(path), exist_ok=True)
+                tmp = path + ".tmp%d" % os.getpid()
+                with open(tmp, "w") as fh:
+                    json.dump(cache, fh, indent=1)
+                os.replace(tmp, path)
+            except OSError:
+                pass
+        return res
+
+    def synchronize(self):
+        with self._dev():
+            _check(load_library().lbm_batch_synchronize(self._h), "lbm_batch_synchronize")
+
+    @property
+    def launch_count(self):
+        return load_library().lbm_batch_launch_count(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            with self._dev():
+                load_library().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

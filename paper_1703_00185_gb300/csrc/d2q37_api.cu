@@ -9,45 +9,24 @@
 #include <cuda_runtime.h>
 
 #include "../../include/d2q37.h"
-#include "d2q37_launch.h"
+#include "d2q37_handle.h"
 
 using namespace d2q37;
-
-struct lbm_t {
-  int Lx, Ly, NX, NY;
-  lbm_params prm;
-  StepParams sp;
-  double* buf[2];
-  int cur;
-  double* scratch;  // 4 Lx Ly doubles: fields, or the initial temperature
-  void* owned;      // cudaMalloc'ed block, NULL for lbm_create_ext
-  cudaStream_t stream;
-  bool owns_stream;
-  bool have_state;
-  bool halo_valid;  // halo columns (and rows, if y is periodic) mirror the current state
-  int64_t launches;
-  cudaGraphExec_t graph2[2];  // two fused steps starting from buffer 0 / 1
-  bool graph_unavailable;
-  // per-kernel timing: event pairs recorded around launches, folded into the
-  // totals when the stream is synchronised
-  bool timing;
-  struct Pending {
-    int kind;
-    cudaEvent_t start, stop;
-  };
-  std::vector<Pending> pending;
-  std::vector<cudaEvent_t> event_pool;
-  double kind_ms[LBM_KIND_COUNT];
-  int64_t kind_launches[LBM_KIND_COUNT];
-};
 
 namespace {
 
 std::once_flag g_quad_once;
 bool g_quad_ok = false;
 ShellConsts g_consts;
+ShellConsts32 g_consts32;
 std::mutex g_dev_mutex;
 bool g_dev_ready[256];
+
+// hi + lo split of a double into two floats (hi = nearest float).
+void split_df(double v, float* hi, float* lo) {
+  *hi = (float)v;
+  *lo = (float)(v - (double)*hi);
+}
 
 void solve_once() {
   double s, w[kShells];
@@ -55,6 +34,13 @@ void solve_once() {
   ShellConsts& c = g_consts;
   c.s = s;
   c.s2 = s * s;
+  ShellConsts32& c32 = g_consts32;
+  c32.s = c.s;
+  c32.s2 = c.s2;
+  split_df(c.s, &c32.s_hi, &c32.s_lo);
+  split_df(c.s2, &c32.s2_hi, &c32.s2_lo);
+  c32.inv_s2 = 1.0 / c.s2;
+  split_df(c32.inv_s2, &c32.inv_s2_hi, &c32.inv_s2_lo);
   for (int k = 0; k < kShells; ++k) {
     const double x2 = c.s2 * shell_c2(k);
     c.w[k] = w[k];
@@ -63,6 +49,12 @@ void solve_once() {
     c.gamma[k] = (x2 * x2 - 8.0 * x2 + 8.0) / 8.0;
     c.delta[k] = (x2 - 4.0) / 2.0;
     c.eps[k] = (x2 - 6.0) / 4.0;
+    c32.x2[k] = x2;
+    split_df(x2, &c32.x2_hi[k], &c32.x2_lo[k]);
+    c32.w64[k] = w[k];
+    c32.w[k] = (float)w[k];
+    c32.delta[k] = (float)c.delta[k];
+    c32.eps[k] = (float)c.eps[k];
   }
   g_quad_ok = true;
 }
@@ -78,6 +70,7 @@ int ensure_device_consts() {
   std::lock_guard<std::mutex> lock(g_dev_mutex);
   if (!g_dev_ready[dev]) {
     if (upload_shell_consts(g_consts) != cudaSuccess) return LBM_ECUDA;
+    if (upload_shell_consts32(g_consts32) != cudaSuccess) return LBM_ECUDA;
     g_dev_ready[dev] = true;
   }
   return LBM_OK;
@@ -85,20 +78,34 @@ int ensure_device_consts() {
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
-int frame_ny(int Ly) { return ((Ly + 2 * kHy) + 15) / 16 * 16; }
+bool is_fp32(int prec) { return prec != LBM_PRECISION_FP64; }
+
+int halo_rows(int prec) { return is_fp32(prec) ? kHy32 : kHy; }
+
+// Column stride: 128-byte multiples (16 doubles or 32 floats).
+int frame_ny(int Ly, int prec) {
+  const int q = is_fp32(prec) ? 32 : 16;
+  return ((Ly + 2 * halo_rows(prec)) + q - 1) / q * q;
+}
+
+size_t elem_bytes(int prec) { return is_fp32(prec) ? sizeof(float) : sizeof(double); }
 
 bool valid_params(int Lx, int Ly, const lbm_params* p) {
   if (!p || Lx < 3 || Ly < 6) return false;
   if (!(p->tau > 0.5) || !std::isfinite(p->tau) || !std::isfinite(p->g0)) return false;
   if (!(p->T_top > 0.0) || !(p->T_bot > 0.0)) return false;
-  if (p->precision != 0) return false;
+  if (p->precision != LBM_PRECISION_FP64 && p->precision != LBM_PRECISION_FP32_FP64 &&
+      p->precision != LBM_PRECISION_FP32_DF)
+    return false;
   if (p->kernel != LBM_KERNEL_SEPARATE && p->kernel != LBM_KERNEL_FUSED) return false;
   if ((long long)Lx * Ly > (1LL << 34)) return false;
+  // one population plane must stay below 2^31 elements (32-bit in-plane offsets)
+  if ((long long)(Lx + 2 * kHx) * frame_ny(Ly, p->precision) >= (1LL << 31)) return false;
   return true;
 }
 
-size_t buffer_bytes(int Lx, int Ly) {
-  return align256((size_t)kQ * (size_t)(Lx + 2 * kHx) * (size_t)frame_ny(Ly) * sizeof(double));
+size_t buffer_bytes(int Lx, int Ly, int prec) {
+  return align256((size_t)kQ * (size_t)(Lx + 2 * kHx) * (size_t)frame_ny(Ly, prec) * elem_bytes(prec));
 }
 
 size_t scratch_bytes(int Lx, int Ly) { return align256((size_t)4 * Lx * Ly * sizeof(double)); }
@@ -109,14 +116,19 @@ void fill_step_params(lbm_t* h) {
   sp.Lx = h->Lx;
   sp.Ly = h->Ly;
   sp.NY = h->NY;
+  sp.Hy = halo_rows(h->prec);
   sp.periodic_y = h->prm.periodic_y ? 1 : 0;
   sp.plane = (long long)h->NX * h->NY;
   const double tau = h->prm.tau;
   sp.omega = 1.0 / tau;
   sp.one_minus_omega = 1.0 - sp.omega;
+  sp.omega_f = (float)sp.omega;
+  sp.keep_f = 1.0f - sp.omega_f;  // exact for omega in (0, 2): keep_f + omega_f == 1
   const double gy = -h->prm.g0;
   sp.uy_shift = tau * gy;
   sp.theta_shift = -(tau * tau * gy * gy) / 2.0 - 1.0;
+  split_df(sp.uy_shift, &sp.uy_shift_df[0], &sp.uy_shift_df[1]);
+  split_df(sp.theta_shift, &sp.theta_shift_df[0], &sp.theta_shift_df[1]);
   const double Tw[2] = {h->prm.T_bot, h->prm.T_top};
   for (int wall = 0; wall < 2; ++wall) {
     equilibrium(g_consts, 1.0, 0.0, 0.0, Tw[wall], sp.fw[wall]);
@@ -177,22 +189,61 @@ int drain_timing(lbm_t* h) {
   return rc;
 }
 
+// ---- kernel dispatch by storage precision -----------------------------------
+
+int k_wrap(lbm_t* h, void* b) {
+  return is_fp32(h->prec) ? launch_wrap32((float*)b, h->sp, h->stream) : launch_wrap((double*)b, h->sp, h->stream);
+}
+
+int k_propagate(lbm_t* h, const void* s, void* d) {
+  return is_fp32(h->prec) ? launch_propagate32((const float*)s, (float*)d, h->sp, h->stream)
+                          : launch_propagate((const double*)s, (double*)d, h->sp, h->stream);
+}
+
+int k_bc(lbm_t* h, const void* s, void* d) {
+  return is_fp32(h->prec) ? launch_bc32((const float*)s, (float*)d, h->sp, h->stream)
+                          : launch_bc((const double*)s, (double*)d, h->sp, h->stream);
+}
+
+int k_collide(lbm_t* h, void* b) {
+  return is_fp32(h->prec) ? launch_collide32((float*)b, h->sp, h->prec == LBM_PRECISION_FP32_FP64, h->stream)
+                          : launch_collide((double*)b, h->sp, h->stream);
+}
+
+int k_fused(lbm_t* h, const void* s, void* d) {
+  return is_fp32(h->prec)
+             ? launch_fused32((const float*)s, (float*)d, h->sp, h->prec == LBM_PRECISION_FP32_FP64, h->stream)
+             : launch_fused((const double*)s, (double*)d, h->sp, h->stream);
+}
+
+int k_fields(lbm_t* h, const void* b, double* rho, double* u, double* T) {
+  return is_fp32(h->prec) ? launch_fields32((const float*)b, rho, u, T, h->sp, h->stream)
+                          : launch_fields((const double*)b, rho, u, T, h->sp, h->stream);
+}
+
+int k_init(lbm_t* h, void* b, const double* T) {
+  return is_fp32(h->prec) ? launch_init_equilibrium32((float*)b, T, h->sp, h->stream)
+                          : launch_init_equilibrium((double*)b, T, h->sp, h->stream);
+}
+
 int setup_handle(lbm_t* h, int Lx, int Ly, const lbm_params* p, void* mem, cudaStream_t stream) {
   h->Lx = Lx;
   h->Ly = Ly;
+  h->prec = p->precision;
+  h->elem = elem_bytes(h->prec);
   h->NX = Lx + 2 * kHx;
-  h->NY = frame_ny(Ly);
+  h->NY = frame_ny(Ly, h->prec);
   h->prm = *p;
-  const size_t bb = buffer_bytes(Lx, Ly);
+  const size_t bb = buffer_bytes(Lx, Ly, h->prec);
   char* base = (char*)mem;
-  h->buf[0] = (double*)base;
-  h->buf[1] = (double*)(base + bb);
+  h->buf[0] = base;
+  h->buf[1] = base + bb;
   h->scratch = (double*)(base + 2 * bb);
   h->cur = 0;
   h->stream = stream;
   fill_step_params(h);
-  // halo rows must read as zero: the pull takes the populations a wall
-  // replaces from there
+  // halo rows must read as zero (FP64) or as f = w (FP32 deviations): the pull
+  // takes the populations a wall replaces from there
   int rc = check(cudaMemsetAsync(base, 0, 2 * bb, stream));
   if (rc == LBM_OK) rc = check(cudaStreamSynchronize(stream));
   return rc;
@@ -210,30 +261,30 @@ uint64_t splitmix64(uint64_t v) {
 int step_once(lbm_t* h, int phases, bool fused) {
   int rc = LBM_OK;
   if (phases & LBM_PHASE_PROPAGATE) {
-    double* src = h->buf[h->cur];
-    double* dst = h->buf[1 - h->cur];
+    void* src = h->buf[h->cur];
+    void* dst = h->buf[1 - h->cur];
     if (!h->halo_valid) {
-      rc = run_kernel(h, LBM_KIND_WRAP, [&] { return launch_wrap(src, h->sp, h->stream); });
+      rc = run_kernel(h, LBM_KIND_WRAP, [&] { return k_wrap(h, src); });
       if (rc) return rc;
       h->halo_valid = true;
     }
     if (fused) {
-      rc = run_kernel(h, LBM_KIND_FUSED, [&] { return launch_fused(src, dst, h->sp, h->stream); });
+      rc = run_kernel(h, LBM_KIND_FUSED, [&] { return k_fused(h, src, dst); });
       if (rc) return rc;
       h->cur = 1 - h->cur;  // fused writes the halo images of dst
       return LBM_OK;
     }
-    rc = run_kernel(h, LBM_KIND_PROPAGATE, [&] { return launch_propagate(src, dst, h->sp, h->stream); });
+    rc = run_kernel(h, LBM_KIND_PROPAGATE, [&] { return k_propagate(h, src, dst); });
     if (rc) return rc;
     if ((phases & LBM_PHASE_BC) && !h->prm.periodic_y) {
-      rc = run_kernel(h, LBM_KIND_BC, [&] { return launch_bc(src, dst, h->sp, h->stream); });
+      rc = run_kernel(h, LBM_KIND_BC, [&] { return k_bc(h, src, dst); });
       if (rc) return rc;
     }
     h->cur = 1 - h->cur;
     h->halo_valid = false;  // propagate writes physical sites only
   }
   if (phases & LBM_PHASE_COLLIDE) {
-    rc = run_kernel(h, LBM_KIND_COLLIDE, [&] { return launch_collide(h->buf[h->cur], h->sp, h->stream); });
+    rc = run_kernel(h, LBM_KIND_COLLIDE, [&] { return k_collide(h, h->buf[h->cur]); });
     if (!rc) h->halo_valid = true;  // collide writes the halo images
   }
   return rc;
@@ -254,8 +305,8 @@ bool fused_pair_graph(lbm_t* h, cudaGraphExec_t* out) {
       h->graph_unavailable = true;
       return false;
     }
-    const int n1 = launch_fused(h->buf[c], h->buf[1 - c], h->sp, h->stream);
-    const int n2 = launch_fused(h->buf[1 - c], h->buf[c], h->sp, h->stream);
+    const int n1 = k_fused(h, h->buf[c], h->buf[1 - c]);
+    const int n2 = k_fused(h, h->buf[1 - c], h->buf[c]);
     const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     if (e != cudaSuccess || n1 < 0 || n2 < 0 || cudaGraphInstantiate(&g, graph, 0) != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -270,7 +321,30 @@ bool fused_pair_graph(lbm_t* h, cudaGraphExec_t* out) {
   return true;
 }
 
+size_t plane_offset_bytes(const lbm_t* h, int l) {
+  return ((size_t)l * h->sp.plane + (size_t)kHx * h->NY + h->sp.Hy) * h->elem;
+}
+
 }  // namespace
+
+namespace d2q37 {
+
+int handle_prepare_halos(lbm_t* h, cudaStream_t stream) {
+  if (h->halo_valid) return LBM_OK;
+  void* b = h->buf[h->cur];
+  const int n = is_fp32(h->prec) ? launch_wrap32((float*)b, h->sp, stream) : launch_wrap((double*)b, h->sp, stream);
+  if (n < 0) return LBM_ECUDA;
+  h->launches += n;
+  h->halo_valid = true;
+  return LBM_OK;
+}
+
+int handle_device_consts() {
+  if (!quadrature_ready()) return LBM_ESTATE;
+  return ensure_device_consts();
+}
+
+}  // namespace d2q37
 
 extern "C" {
 
@@ -280,7 +354,7 @@ void lbm_default_params(lbm_params* p) {
   p->g0 = 1e-4;
   p->T_top = 0.5;
   p->T_bot = 1.5;
-  p->precision = 0;
+  p->precision = LBM_PRECISION_FP64;
   p->kernel = LBM_KERNEL_FUSED;
   p->periodic_y = 0;
 }
@@ -304,7 +378,7 @@ int lbm_quadrature(double* s, double* w) {
 
 size_t lbm_required_bytes(int Lx, int Ly, const lbm_params* p) {
   if (!valid_params(Lx, Ly, p)) return 0;
-  return 2 * buffer_bytes(Lx, Ly) + scratch_bytes(Lx, Ly);
+  return 2 * buffer_bytes(Lx, Ly, p->precision) + scratch_bytes(Lx, Ly);
 }
 
 int lbm_create(int Lx, int Ly, const lbm_params* p, lbm_t** out) {
@@ -371,10 +445,8 @@ int lbm_init_rayleigh_taylor(lbm_t* h, uint64_t seed) {
   }
   int rc = check(cudaMemcpyAsync(h->scratch, T.data(), T.size() * sizeof(double), cudaMemcpyHostToDevice,
                                  h->stream));
-  if (!rc) rc = check(cudaMemsetAsync(h->buf[h->cur], 0, buffer_bytes(Lx, Ly), h->stream));
-  if (!rc)
-    rc = run_kernel(h, LBM_KIND_INIT,
-                    [&] { return launch_init_equilibrium(h->buf[h->cur], h->scratch, h->sp, h->stream); });
+  if (!rc) rc = check(cudaMemsetAsync(h->buf[h->cur], 0, buffer_bytes(Lx, Ly, h->prec), h->stream));
+  if (!rc) rc = run_kernel(h, LBM_KIND_INIT, [&] { return k_init(h, h->buf[h->cur], h->scratch); });
   if (!rc) rc = check(cudaStreamSynchronize(h->stream));
   if (!rc) {
     h->have_state = true;
@@ -385,13 +457,26 @@ int lbm_init_rayleigh_taylor(lbm_t* h, uint64_t seed) {
 
 int lbm_set_populations(lbm_t* h, const double* f) {
   if (!h || !f) return LBM_EINVAL;
-  double* d = h->buf[h->cur];
+  char* d = (char*)h->buf[h->cur];
+  const size_t n = (size_t)h->Lx * h->Ly;
   for (int l = 0; l < kQ; ++l) {
-    const cudaError_t e = cudaMemcpy2DAsync(d + l * h->sp.plane + (size_t)kHx * h->NY + kHy, h->NY * sizeof(double),
-                                            f + (size_t)l * h->Lx * h->Ly, h->Ly * sizeof(double),
-                                            h->Ly * sizeof(double), h->Lx, cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) return LBM_ECUDA;
+    if (!is_fp32(h->prec)) {
+      if (cudaMemcpy2DAsync(d + plane_offset_bytes(h, l), h->NY * sizeof(double), f + (size_t)l * n,
+                            h->Ly * sizeof(double), h->Ly * sizeof(double), h->Lx, cudaMemcpyHostToDevice,
+                            h->stream) != cudaSuccess)
+        return LBM_ECUDA;
+      continue;
+    }
+    // FP32 storage: stage the FP64 plane in scratch, convert to deviations on the device
+    if (cudaMemcpyAsync(h->scratch, f + (size_t)l * n, n * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
+        cudaSuccess)
+      return LBM_ECUDA;
+    const int rc = run_kernel(h, LBM_KIND_CONVERT, [&] {
+      return launch_plane_to_frame32((float*)h->buf[h->cur], h->scratch, l, h->sp, h->stream);
+    });
+    if (rc) return rc;
   }
+  if (is_fp32(h->prec) && cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ECUDA;
   h->have_state = true;
   h->halo_valid = false;
   return LBM_OK;
@@ -400,12 +485,23 @@ int lbm_set_populations(lbm_t* h, const double* f) {
 int lbm_get_populations(lbm_t* h, double* f) {
   if (!h || !f) return LBM_EINVAL;
   if (!h->have_state) return LBM_ESTATE;
-  const double* d = h->buf[h->cur];
+  const char* d = (const char*)h->buf[h->cur];
+  const size_t n = (size_t)h->Lx * h->Ly;
   for (int l = 0; l < kQ; ++l) {
-    const cudaError_t e = cudaMemcpy2DAsync(f + (size_t)l * h->Lx * h->Ly, h->Ly * sizeof(double),
-                                            d + l * h->sp.plane + (size_t)kHx * h->NY + kHy, h->NY * sizeof(double),
-                                            h->Ly * sizeof(double), h->Lx, cudaMemcpyDeviceToHost, h->stream);
-    if (e != cudaSuccess) return LBM_ECUDA;
+    if (!is_fp32(h->prec)) {
+      if (cudaMemcpy2DAsync(f + (size_t)l * n, h->Ly * sizeof(double), d + plane_offset_bytes(h, l),
+                            h->NY * sizeof(double), h->Ly * sizeof(double), h->Lx, cudaMemcpyDeviceToHost,
+                            h->stream) != cudaSuccess)
+        return LBM_ECUDA;
+      continue;
+    }
+    const int rc = run_kernel(h, LBM_KIND_CONVERT, [&] {
+      return launch_frame32_to_plane(h->scratch, (const float*)h->buf[h->cur], l, h->sp, h->stream);
+    });
+    if (rc) return rc;
+    if (cudaMemcpyAsync(f + (size_t)l * n, h->scratch, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) !=
+        cudaSuccess)
+      return LBM_ECUDA;
   }
   return check(cudaStreamSynchronize(h->stream));
 }
@@ -449,7 +545,7 @@ int lbm_run_phases(lbm_t* h, int n, int phases) {
 int lbm_fields_device(lbm_t* h, double* rho, double* u, double* T) {
   if (!h || !rho || !u || !T) return LBM_EINVAL;
   if (!h->have_state) return LBM_ESTATE;
-  return run_kernel(h, LBM_KIND_FIELDS, [&] { return launch_fields(h->buf[h->cur], rho, u, T, h->sp, h->stream); });
+  return run_kernel(h, LBM_KIND_FIELDS, [&] { return k_fields(h, h->buf[h->cur], rho, u, T); });
 }
 
 int lbm_fields(lbm_t* h, double* rho, double* u, double* T) {

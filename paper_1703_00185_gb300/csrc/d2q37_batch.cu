@@ -1,0 +1,270 @@
+// Batched stepping of many independent lattices in one launch per step
+// (C ABI declared in include/d2q37.h, lbm_batch_*).
+//
+// The lattices keep their own memory and parameters (lbm_t handles); the
+// batch owns a device table of BatchEntry (parameters, both buffers, the
+// buffer holding the state, tile range) and advances every lattice by one
+// step per launch of the batched fused kernel, walking the tiles of all
+// lattices with a grid-stride loop.  lbm_batch_step(n) replays a captured
+// two-step CUDA graph when the stream can be captured.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "d2q37_handle.h"
+
+struct lbm_batch_t {
+  int n;
+  int prec;
+  std::vector<lbm_t*> lat;
+  std::vector<BatchEntry> host_tab[3];  // per block_y choice (64, 128, 256)
+  BatchEntry* dev_tab[3];
+  long long tiles[3];
+  int block_y;        // 64, 128 or 256
+  int blocks_per_sm;  // 0: one block per tile; else a persistent grid of blocks_per_sm x SMs
+  int sms;
+  int parity;         // lattice i holds its state in buffer entry.cur ^ parity
+  cudaStream_t stream;
+  int64_t launches;
+  cudaGraphExec_t graph2;  // two steps from parity 0
+  int graph_config;        // block_y * 16 + blocks_per_sm the graph was captured with
+  bool graph_unavailable;
+};
+
+namespace {
+
+int check(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
+
+int slot_of(int block_y) { return block_y == 64 ? 0 : block_y == 128 ? 1 : block_y == 256 ? 2 : -1; }
+
+int max_blocks_per_sm(const lbm_batch_t* b, int block_y) {
+  return b->prec == LBM_PRECISION_FP64 ? batch_blocks_per_sm(block_y)
+                                       : batch32_blocks_per_sm(block_y, b->prec == LBM_PRECISION_FP32_FP64);
+}
+
+long long grid_of(const lbm_batch_t* b, int block_y, int blocks_per_sm) {
+  const long long tiles = b->tiles[slot_of(block_y)];
+  long long g = blocks_per_sm > 0 ? (long long)blocks_per_sm * b->sms : tiles;
+  g = std::min(g, tiles);
+  return std::min(std::max(g, 1LL), 2147483647LL);
+}
+
+int launch(lbm_batch_t* b, int block_y, int blocks_per_sm, int parity) {
+  const int s = slot_of(block_y);
+  const int grid = (int)grid_of(b, block_y, blocks_per_sm);
+  const int n = b->prec == LBM_PRECISION_FP64
+                    ? launch_batch_fused(b->dev_tab[s], b->n, b->tiles[s], parity, block_y, grid, b->stream)
+                    : launch_batch_fused32(b->dev_tab[s], b->n, b->tiles[s], parity, block_y, grid,
+                                           b->prec == LBM_PRECISION_FP32_FP64, b->stream);
+  if (n < 0) return LBM_ECUDA;
+  b->launches += n;
+  return LBM_OK;
+}
+
+// Record the parity of the lattices' current buffers in their handles.
+void publish_parity(lbm_batch_t* b) {
+  for (int i = 0; i < b->n; ++i) b->lat[i]->cur = b->host_tab[0][i].cur ^ b->parity;
+}
+
+bool pair_graph(lbm_batch_t* b, cudaGraphExec_t* out) {
+  if (b->graph_unavailable) return false;
+  const int cfg = b->block_y * 16 + b->blocks_per_sm;
+  if (b->graph2 && b->graph_config != cfg) {
+    cudaGraphExecDestroy(b->graph2);
+    b->graph2 = nullptr;
+  }
+  if (!b->graph2) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      b->graph_unavailable = true;
+      return false;
+    }
+    const int64_t before = b->launches;
+    const int r0 = launch(b, b->block_y, b->blocks_per_sm, 0);
+    const int r1 = launch(b, b->block_y, b->blocks_per_sm, 1);
+    b->launches = before;
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || r0 || r1 || cudaGraphInstantiate(&b->graph2, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      b->graph2 = nullptr;
+      b->graph_unavailable = true;
+      return false;
+    }
+    cudaGraphDestroy(g);
+    b->graph_config = cfg;
+  }
+  *out = b->graph2;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(int n, lbm_t* const* lattices, void* cuda_stream, lbm_batch_t** out) {
+  if (!out || n <= 0 || !lattices) return LBM_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!lattices[i]) return LBM_EINVAL;
+    if (lattices[i]->prec != lattices[0]->prec) return LBM_EINVAL;
+    if (!lattices[i]->have_state) return LBM_ESTATE;
+    for (int j = 0; j < i; ++j)
+      if (lattices[j] == lattices[i]) return LBM_EINVAL;
+  }
+  int rc = handle_device_consts();
+  if (rc) return rc;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return LBM_ECUDA;
+  lbm_batch_t* b = new lbm_batch_t();
+  b->n = n;
+  b->prec = lattices[0]->prec;
+  b->lat.assign(lattices, lattices + n);
+  b->sms = sms;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->block_y = 128;
+  b->blocks_per_sm = 0;
+  // the lattices' own pending work comes first; their halos must mirror the state
+  for (int i = 0; i < n && !rc; ++i) {
+    rc = check(cudaStreamSynchronize(lattices[i]->stream));
+    if (!rc) rc = handle_prepare_halos(lattices[i], b->stream);
+  }
+  const int bys[3] = {64, 128, 256};
+  for (int s = 0; s < 3 && !rc; ++s) {
+    long long t0 = 0;
+    b->host_tab[s].resize(n);
+    for (int i = 0; i < n; ++i) {
+      BatchEntry& e = b->host_tab[s][i];
+      std::memset(&e, 0, sizeof(e));
+      e.p = lattices[i]->sp;
+      e.buf[0] = lattices[i]->buf[0];
+      e.buf[1] = lattices[i]->buf[1];
+      e.cur = lattices[i]->cur;
+      e.ytiles = (lattices[i]->Ly + bys[s] - 1) / bys[s];
+      e.tile0 = t0;
+      t0 += (long long)lattices[i]->Lx * e.ytiles;
+    }
+    b->tiles[s] = t0;
+    if (cudaMalloc(&b->dev_tab[s], n * sizeof(BatchEntry)) != cudaSuccess) {
+      cudaGetLastError();
+      rc = LBM_ENOMEM;
+      break;
+    }
+    rc = check(cudaMemcpyAsync(b->dev_tab[s], b->host_tab[s].data(), n * sizeof(BatchEntry),
+                               cudaMemcpyHostToDevice, b->stream));
+  }
+  if (!rc) rc = check(cudaStreamSynchronize(b->stream));
+  if (rc) {
+    lbm_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_set_config(lbm_batch_t* b, int block_y, int blocks_per_sm) {
+  if (!b || slot_of(block_y) < 0 || blocks_per_sm < 0) return LBM_EINVAL;
+  if (blocks_per_sm > 0 && blocks_per_sm > max_blocks_per_sm(b, block_y)) return LBM_EINVAL;
+  b->block_y = block_y;
+  b->blocks_per_sm = blocks_per_sm;
+  return LBM_OK;
+}
+
+int lbm_batch_get_config(const lbm_batch_t* b, int* block_y, int* blocks_per_sm) {
+  if (!b || !block_y || !blocks_per_sm) return LBM_EINVAL;
+  *block_y = b->block_y;
+  *blocks_per_sm = b->blocks_per_sm;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch_t* b, int n) {
+  if (!b || n < 0) return LBM_EINVAL;
+  int t = 0;
+  if (n >= 4) {
+    if (b->parity) {
+      const int rc = launch(b, b->block_y, b->blocks_per_sm, b->parity);
+      if (rc) return rc;
+      b->parity ^= 1;
+      ++t;
+    }
+    cudaGraphExec_t g;
+    while (n - t >= 2 && pair_graph(b, &g)) {
+      if (cudaGraphLaunch(g, b->stream) != cudaSuccess) return LBM_ECUDA;
+      b->launches += 2;
+      t += 2;
+    }
+  }
+  for (; t < n; ++t) {
+    const int rc = launch(b, b->block_y, b->blocks_per_sm, b->parity);
+    if (rc) return rc;
+    b->parity ^= 1;
+  }
+  publish_parity(b);
+  return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch_t* b, int trial_steps, int* block_y, int* blocks_per_sm, double* best_ms) {
+  if (!b || trial_steps <= 0) return LBM_EINVAL;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return LBM_ECUDA;
+  }
+  int rc = LBM_OK;
+  float best = 1e30f;
+  int best_by = b->block_y, best_bps = b->blocks_per_sm;
+  const int bys[3] = {64, 128, 256};
+  const int64_t launches0 = b->launches;
+  for (int s = 0; s < 3 && !rc; ++s) {
+    const int occ = max_blocks_per_sm(b, bys[s]);
+    for (int bps = 0; bps <= occ && !rc; ++bps) {
+      // the same parity every launch: each trial recomputes the same step into
+      // the other buffer, so the lattices' state does not advance
+      rc = launch(b, bys[s], bps, b->parity);
+      if (!rc) rc = check(cudaEventRecord(e0, b->stream));
+      for (int k = 0; k < trial_steps && !rc; ++k) rc = launch(b, bys[s], bps, b->parity);
+      if (!rc) rc = check(cudaEventRecord(e1, b->stream));
+      if (!rc) rc = check(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      if (!rc) rc = check(cudaEventElapsedTime(&ms, e0, e1));
+      if (!rc && ms < best) {
+        best = ms;
+        best_by = bys[s];
+        best_bps = bps;
+      }
+    }
+  }
+  b->launches = launches0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  b->block_y = best_by;
+  b->blocks_per_sm = best_bps;
+  if (block_y) *block_y = best_by;
+  if (blocks_per_sm) *blocks_per_sm = best_bps;
+  if (best_ms) *best_ms = best / trial_steps;
+  return LBM_OK;
+}
+
+int lbm_batch_synchronize(lbm_batch_t* b) {
+  if (!b) return LBM_EINVAL;
+  return check(cudaStreamSynchronize(b->stream));
+}
+
+int64_t lbm_batch_launch_count(const lbm_batch_t* b) { return b ? b->launches : 0; }
+
+void lbm_batch_destroy(lbm_batch_t* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph2) cudaGraphExecDestroy(b->graph2);
+  for (BatchEntry* t : b->dev_tab)
+    if (t) cudaFree(t);
+  delete b;
+}
+
+}  // extern "C"

@@ -46,8 +46,8 @@ __device__ __forceinline__ long long site_index(const StepParams& p, int x, int 
 // rho, u and T of one site (Sec. "Lattice Boltzmann methods"):
 // rho = sum f, rho u = s sum c f, D rho T = sum |xi|^2 f - rho |u|^2 (D = 2),
 // the last being sum |xi - u|^2 f expanded.  Pair sums and differences carry
-// the even and odd moments.  FP64 arithmetic throughout (reference form, and
-// the fallback of site_moments_fixed).
+// the even and odd moments.  FP64 arithmetic throughout (the fallback of
+// site_moments below).
 __device__ __forceinline__ void site_moments_fp64(const double (&f)[kQ], double& rho, double& ux, double& uy,
                                                   double& T) {
   double sh[kShells];
@@ -304,11 +304,10 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) collide_kernel
   store_site(buf, p, x, y, f);
 }
 
-__global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(const double* __restrict__ src, double* __restrict__ dst,
-                                                        StepParams p) {
-  const int x = blockIdx.x;
-  const int y = blockIdx.y * kBlockY + threadIdx.x;
-  if (y >= p.Ly) return;
+// One site of the fused step: gather (pull), wall bc on the wall bands,
+// collide, store with halo images.
+__device__ __forceinline__ void fused_site(const double* __restrict__ src, double* __restrict__ dst,
+                                           const StepParams& p, int x, int y) {
   const long long i = site_index(p, x, y);
   double f[kQ];
 #pragma unroll
@@ -325,6 +324,31 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(c
   }
   collide_site(f, p);
   store_site(dst, p, x, y, f);
+}
+
+__global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                                        StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  fused_site(src, dst, p, x, y);
+}
+
+// Many lattices in one launch: block-sized tiles (one column x, BY
+// consecutive y) of every lattice in the table, walked by a grid-stride loop
+// (persistent when the grid is sized to the resident blocks).  Lattice i
+// reads buffer cur_i ^ parity and writes the other one.
+template <int BY>
+__global__ void __launch_bounds__(BY, (D2Q37_SITE_MIN_BLOCKS * 128) / BY) batch_fused_kernel(
+    const BatchEntry* __restrict__ tab, int n, long long tiles, int parity) {
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const BatchEntry& e = tab[batch_entry_of(tab, n, t)];
+    const long long local = t - e.tile0;
+    const int x = (int)(local / e.ytiles);
+    const int y = (int)(local - (long long)x * e.ytiles) * BY + threadIdx.x;
+    const int c = e.cur ^ parity;
+    if (y < e.p.Ly) fused_site((const double*)e.buf[c], (double*)e.buf[c ^ 1], e.p, x, y);
+  }
 }
 
 __global__ void __launch_bounds__(kBlockY) fields_kernel(const double* __restrict__ buf, double* __restrict__ rho,
@@ -409,6 +433,38 @@ int launch_collide(double* buf, const StepParams& p, cudaStream_t stream) {
 int launch_fused(const double* src, double* dst, const StepParams& p, cudaStream_t stream) {
   fused_kernel<<<site_grid(p), kBlockY, 0, stream>>>(src, dst, p);
   return done(1);
+}
+
+template <int BY>
+int batch_launch(const BatchEntry* tab, int n, long long tiles, int parity, int grid, cudaStream_t stream) {
+  batch_fused_kernel<BY><<<grid, BY, 0, stream>>>(tab, n, tiles, parity);
+  return done(1);
+}
+
+template <int BY>
+int batch_occupancy() {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_fused_kernel<BY>, BY, 0);
+  return b;
+}
+
+int launch_batch_fused(const BatchEntry* tab, int n, long long tiles, int parity, int block_y, int grid,
+                       cudaStream_t stream) {
+  switch (block_y) {
+    case 64: return batch_launch<64>(tab, n, tiles, parity, grid, stream);
+    case 128: return batch_launch<128>(tab, n, tiles, parity, grid, stream);
+    case 256: return batch_launch<256>(tab, n, tiles, parity, grid, stream);
+    default: return -1;
+  }
+}
+
+int batch_blocks_per_sm(int block_y) {
+  switch (block_y) {
+    case 64: return batch_occupancy<64>();
+    case 128: return batch_occupancy<128>();
+    case 256: return batch_occupancy<256>();
+    default: return 0;
+  }
 }
 
 int launch_fields(const double* buf, double* rho, double* u, double* T, const StepParams& p, cudaStream_t stream) {

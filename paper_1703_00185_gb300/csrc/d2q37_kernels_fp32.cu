@@ -1,0 +1,597 @@
+// sm_103a kernels of the D2Q37 step with FP32 deviation storage.
+//
+// Populations are stored as d_l = f_l - w_l in FP32 (half the HBM bytes of
+// FP64: 296 B per site update).  Precision split, per site:
+//   * moment sums (density, momentum, energy): exact 64-bit integer sums of
+//     the stored FP32 values (no rounding in the additions);
+//   * rho, u, T and the temperature-dependent part of the equilibrium,
+//     G0_k = rho C0_k - 1 per shell (where theta-terms cancel near T = 0.5),
+//     in a "wide" type: FP64, or double-float on the FP32 pipes;
+//   * the velocity-dependent part of each population pair and the relaxation
+//     in FP32, with d' = (1 - omega) d + omega w (rho P - 1).
+// Layout and step sequence are those of the FP64 kernels (d2q37_kernels.cu)
+// with 32 halo rows so FP32 columns stay 128-byte aligned.
+#include <cuda_runtime.h>
+
+#include "d2q37_launch.h"
+#include "dfloat.cuh"
+
+namespace d2q37 {
+
+__constant__ ShellConsts32 c_shell32;
+
+namespace {
+
+constexpr int kBlockY = 128;
+
+#ifndef D2Q37_FP32_MIN_BLOCKS
+#define D2Q37_FP32_MIN_BLOCKS 4
+#endif
+
+__device__ __forceinline__ long long site_index(const StepParams& p, int x, int y) {
+  return (long long)(x + kHx) * p.NY + (y + p.Hy);
+}
+
+// ---- the wide type: FP64 or double-float, behind one set of names ----------
+
+struct WideF64 {
+  using T = double;
+  static __device__ __forceinline__ T from_fixed(long long v, int e) { return (double)v * exp2_d(e); }
+  static __device__ __forceinline__ double exp2_d(int e) { return __hiloint2double((e + 1023) << 20, 0); }
+  static __device__ __forceinline__ T c(double hi, float, float) { return hi; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T add(T a, float b) { return a + (double)b; }
+  static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T mul(T a, float b) { return a * (double)b; }
+  static __device__ __forceinline__ T rcp(T a) { return 1.0 / a; }
+  static __device__ __forceinline__ float tof(T a) { return (float)a; }
+};
+
+struct WideDF {
+  using T = dfloat;
+  static __device__ __forceinline__ T from_fixed(long long v, int e) { return df_from_int64(v, e); }
+  static __device__ __forceinline__ T c(double, float hi, float lo) { return {hi, lo}; }
+  // about 44 bits: far more than the ~30 the FP32-storage step needs here
+  static __device__ __forceinline__ T add(T a, T b) { return df_add_fast(a, b); }
+  static __device__ __forceinline__ T add(T a, float b) { return df_add(a, b); }
+  static __device__ __forceinline__ T sub(T a, T b) { return df_add_fast(a, df_neg(b)); }
+  static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
+  static __device__ __forceinline__ T mul(T a, float b) { return df_mul(a, b); }
+  static __device__ __forceinline__ T rcp(T a) { return df_rcp(a); }
+  static __device__ __forceinline__ float tof(T a) { return df_to_float(a); }
+};
+
+// ---- moment sums of the stored deviations in integer arithmetic ------------
+
+// Fast path (|d| < 1.5 at every population): each deviation is split with two
+// float additions of "magic" constants into d ~ (hi 2^22 + lo) 2^-43 with
+// integers |hi| < 2^22, |lo| <= 2^21 (error <= 2^-44, none at all for
+// |d| >= 2^-20): t1 = d + 6 has an ulp of 2^-21, so its bit pattern minus that
+// of 6 is hi = round(d 2^21) and d - (t1 - 6) is exact; the remainder gets the
+// same treatment around 1.5 2^-20 (ulp 2^-43).  The moment sums (37 terms,
+// weights |c|^2 <= 10) are then exact sums of 32-bit integers, all on the
+// integer and FP32 pipes (a float-to-int64 conversion would use the FP64 pipe).
+// Other sites (|d| >= 2, non-finite) take the exact 64-bit conversion.
+constexpr int kFixExp = -43;
+
+struct Sums {
+  long long s, jx, jy, e;  // sum d, sum cx d, sum cy d, sum |c|^2 d on the grid 2^ex
+  int ex;
+  bool ok;
+};
+
+struct Split {
+  int hi, lo;
+};
+
+__device__ __forceinline__ Split split_deviation(float v) {
+  const float m1 = 6.0f, m2 = 0x1.8p-20f;
+  const float t1 = __fadd_rn(v, m1);
+  const float r = __fsub_rn(v, __fsub_rn(t1, m1));
+  const float t2 = __fadd_rn(r, m2);
+  return {__float_as_int(t1) - __float_as_int(m1), __float_as_int(t2) - __float_as_int(m2)};
+}
+
+__device__ __forceinline__ long long join(int hi, int lo) { return (long long)hi * (1LL << 22) + lo; }
+
+__device__ __forceinline__ Sums deviation_sums_wide(const float (&d)[kQ]) {
+  // |d| < 16: d 2^43 is an integer below 2^47 for |d| >= 2^-20; sums < 2^63
+  Sums r;
+  r.ex = kFixExp;
+  long long sh[kShells];
+  sh[0] = __float2ll_rn(d[0] * 0x1p43f);
+#pragma unroll
+  for (int k = 1; k < kShells; ++k) sh[k] = 0;
+  long long jx = 0, jy = 0;
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    const long long vp = __float2ll_rn(d[1 + 2 * p] * 0x1p43f);
+    const long long vm = __float2ll_rn(d[2 + 2 * p] * 0x1p43f);
+    sh[pair_shell(p)] += vp + vm;
+    jx += pair_cx(p) * (vp - vm);
+    jy += pair_cy(p) * (vp - vm);
+  }
+  long long s = sh[0], e = 0;
+#pragma unroll
+  for (int k = 1; k < kShells; ++k) {
+    s += sh[k];
+    e += shell_c2(k) * sh[k];
+  }
+  r.s = s;
+  r.jx = jx;
+  r.jy = jy;
+  r.e = e;
+  return r;
+}
+
+__device__ __forceinline__ Sums deviation_sums(const float (&d)[kQ]) {
+  float amax = 0.0f;
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) amax = fmaxf(amax, fabsf(d[l]));
+  if (!(amax < 1.5f)) {  // keeps d + 6 inside [4, 8) after rounding
+    Sums r = deviation_sums_wide(d);
+    r.ok = amax < 16.0f;  // false for NaN
+    return r;
+  }
+  int sh_hi[kShells], sh_lo[kShells];
+  {
+    const Split v = split_deviation(d[0]);
+    sh_hi[0] = v.hi;
+    sh_lo[0] = v.lo;
+  }
+#pragma unroll
+  for (int k = 1; k < kShells; ++k) sh_hi[k] = sh_lo[k] = 0;
+  int jx_hi = 0, jx_lo = 0, jy_hi = 0, jy_lo = 0;
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    const Split vp = split_deviation(d[1 + 2 * p]);
+    const Split vm = split_deviation(d[2 + 2 * p]);
+    const int k = pair_shell(p);
+    sh_hi[k] += vp.hi + vm.hi;
+    sh_lo[k] += vp.lo + vm.lo;
+    const int dh = vp.hi - vm.hi, dl = vp.lo - vm.lo;
+    jx_hi += pair_cx(p) * dh;
+    jx_lo += pair_cx(p) * dl;
+    jy_hi += pair_cy(p) * dh;
+    jy_lo += pair_cy(p) * dl;
+  }
+  int s_hi = sh_hi[0], s_lo = sh_lo[0], e_hi = 0, e_lo = 0;
+#pragma unroll
+  for (int k = 1; k < kShells; ++k) {
+    s_hi += sh_hi[k];
+    s_lo += sh_lo[k];
+    e_hi += shell_c2(k) * sh_hi[k];
+    e_lo += shell_c2(k) * sh_lo[k];
+  }
+  Sums r;
+  r.ok = true;
+  r.ex = kFixExp;
+  r.s = join(s_hi, s_lo);
+  r.jx = join(jx_hi, jx_lo);
+  r.jy = join(jy_hi, jy_lo);
+  r.e = join(e_hi, e_lo);
+  return r;
+}
+
+// ---- one site ---------------------------------------------------------------
+
+template <class W>
+struct SiteScalars {
+  typename W::T rho, ux, uy, T, E;  // E = sum |xi|^2 f
+};
+
+// rho = 1 + sum d, rho u = s sum c d, 2 rho T = 2 + s^2 sum |c|^2 d - rho |u|^2
+// (sum_l w_l = 1, sum_l w_l c_l = 0, sum_l w_l |xi_l|^2 = D = 2 by the quadrature).
+template <class W>
+__device__ __forceinline__ SiteScalars<W> site_scalars(const float (&d)[kQ]) {
+  using T = typename W::T;
+  const ShellConsts32& c = c_shell32;
+  SiteScalars<W> o;
+  Sums sm = deviation_sums(d);
+  if (!sm.ok) {  // a deviation of 16 or more (or non-finite): fall back to FP32 sums
+    float s = 0.f, jx = 0.f, jy = 0.f, e = 0.f;
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      s += d[l];
+      jx += vel_cx(l) * d[l];
+      jy += vel_cy(l) * d[l];
+      e += (vel_cx(l) * vel_cx(l) + vel_cy(l) * vel_cy(l)) * d[l];
+    }
+    o.rho = W::add(W::c(1.0, 1.0f, 0.0f), s);
+    const T inv = W::rcp(o.rho);
+    const T si = W::mul(inv, W::c(c.s, c.s_hi, c.s_lo));
+    o.ux = W::mul(si, W::c(jx, jx, 0.0f));
+    o.uy = W::mul(si, W::c(jy, jy, 0.0f));
+    const T E = W::add(W::c(2.0, 2.0f, 0.0f), W::mul(W::c(c.s2, c.s2_hi, c.s2_lo), e));
+    const T u2 = W::add(W::mul(o.ux, o.ux), W::mul(o.uy, o.uy));
+    o.T = W::mul(W::sub(W::mul(E, inv), u2), 0.5f);
+    o.E = E;
+    return o;
+  }
+  o.rho = W::add(W::c(1.0, 1.0f, 0.0f), W::from_fixed(sm.s, sm.ex));
+  const T inv = W::rcp(o.rho);
+  const T si = W::mul(inv, W::c(c.s, c.s_hi, c.s_lo));
+  o.ux = W::mul(si, W::from_fixed(sm.jx, sm.ex));
+  o.uy = W::mul(si, W::from_fixed(sm.jy, sm.ex));
+  const T E = W::add(W::c(2.0, 2.0f, 0.0f), W::mul(W::c(c.s2, c.s2_hi, c.s2_lo), W::from_fixed(sm.e, sm.ex)));
+  const T u2 = W::add(W::mul(o.ux, o.ux), W::mul(o.uy, o.uy));
+  o.T = W::mul(W::sub(W::mul(E, inv), u2), 0.5f);
+  o.E = E;
+  return o;
+}
+
+// BGK collision of one site in deviation form:
+//   d_l' = (1 - omega) d_l + omega w_l (rho P_l - 1),
+//   rho P - 1 = G0_k + rho b (C2_k + b/24) +- rho a (C1_k + b/6), b = a^2,
+// with the shifted fields of Eq. MASTERSHIFT3 and G0_k = rho C0_k - 1 written
+// as K0 + x2_k (K1 + x2_k K2) (C0 is quadratic in x2 = |xi|^2).
+template <class W>
+__device__ __forceinline__ void collide_site32(float (&d)[kQ], const StepParams& p) {
+  using T = typename W::T;
+  const ShellConsts32& c = c_shell32;
+  const SiteScalars<W> sc = site_scalars<W>(d);
+  const T uby = W::add(sc.uy, W::c(p.uy_shift, p.uy_shift_df[0], p.uy_shift_df[1]));
+  const T q = W::add(W::mul(sc.ux, sc.ux), W::mul(uby, uby));
+  const T th = W::add(sc.T, W::c(p.theta_shift, p.theta_shift_df[0], p.theta_shift_df[1]));
+  const T th2 = W::mul(th, th);
+  // energy change of the collision in c-units, sum |c|^2 (d' - d) =
+  // omega (E_eq - E) / s^2 with E_eq = rho (|u_bar|^2 + D T_bar)
+  const T Eeq = W::mul(sc.rho, W::add(q, W::mul(W::add(th, W::c(1.0, 1.0f, 0.0f)), 2.0f)));
+  const float target_e = p.omega_f * W::tof(W::mul(W::sub(Eeq, sc.E), W::c(c.inv_s2, c.inv_s2_hi, c.inv_s2_lo)));
+  const T thq = W::mul(th, q);
+  // A0 = 1 - q/2 + q^2/8
+  const T A0 = W::add(W::c(1.0, 1.0f, 0.0f), W::mul(q, W::add(W::c(-0.5, -0.5f, 0.0f), W::mul(q, 0.125f))));
+  // rho C0 - 1 = K0 + K1 x2 + K2 x2^2
+  const T K0 = W::add(W::mul(sc.rho, W::add(W::add(W::sub(A0, th), thq), th2)), W::c(-1.0, -1.0f, 0.0f));
+  const T K1 = W::mul(sc.rho, W::sub(W::sub(W::mul(th, 0.5f), W::mul(thq, 0.25f)), th2));
+  const T K2 = W::mul(W::mul(sc.rho, th2), 0.125f);
+  float G0[kShells];
+#pragma unroll
+  for (int k = 0; k < kShells; ++k) {
+    const T x2 = W::c(c.x2[k], c.x2_hi[k], c.x2_lo[k]);
+    G0[k] = W::tof(W::add(K0, W::mul(x2, W::add(K1, W::mul(x2, K2)))));
+  }
+  const float rho = W::tof(sc.rho);
+  const float thf = W::tof(th);
+  const float qf = W::tof(q);
+  const float sux = W::tof(W::mul(sc.ux, W::c(c.s, c.s_hi, c.s_lo)));
+  const float suy = W::tof(W::mul(uby, W::c(c.s, c.s_hi, c.s_lo)));
+  const float B1 = fmaf(-0.5f, qf, 1.0f);
+  const float B2 = fmaf(-0.25f, qf, 0.5f);
+  const float keep = p.keep_f;
+  // Collision conserves mass exactly (sum_l w_l P_l = 1).  With FP32 weights
+  // and rounding that sum is off by ~1e-8 per site and step, always with the
+  // same sign, which would make the mass drift (likewise the energy).  So the
+  // rest population takes the mass-conserving value
+  // d_0' = d_0 - sum_{l>0} (d_l' - d_l), equal to (1 - omega) d_0 +
+  // omega w_0 G0_0 in exact arithmetic.
+  float moved = 0.0f, moved_e = 0.0f;
+#pragma unroll
+  for (int k = 1; k < kShells; ++k) {
+    float moved_k = 0.0f;
+    const float ow = p.omega_f * c.w[k];
+    const float rC1 = rho * fmaf(thf, c.delta[k], B1);
+    const float rC2 = rho * fmaf(thf, c.eps[k], B2);
+    const float r6 = rho * (1.0f / 6.0f), r24 = rho * (1.0f / 24.0f);
+#pragma unroll
+    for (int pr = 0; pr < kPairs; ++pr) {
+      if (pair_shell(pr) != k) continue;
+      const int cx = pair_cx(pr), cy = pair_cy(pr);
+      const float a = cx == 0 ? cy * suy : (cy == 0 ? cx * sux : fmaf((float)cx, sux, cy * suy));
+      const float b = a * a;
+      const float even = b * fmaf(b, r24, rC2);
+      const float odd = a * fmaf(b, r6, rC1);
+      const float np = fmaf(keep, d[1 + 2 * pr], ow * (G0[k] + even + odd));
+      const float nm = fmaf(keep, d[2 + 2 * pr], ow * (G0[k] + even - odd));
+      moved_k += (np - d[1 + 2 * pr]) + (nm - d[2 + 2 * pr]);
+      d[1 + 2 * pr] = np;
+      d[2 + 2 * pr] = nm;
+    }
+    moved += moved_k;
+    moved_e = fmaf((float)shell_c2(k), moved_k, moved_e);
+  }
+  // Same for energy: the rounding residue of sum |c|^2 (d' - d) goes evenly
+  // to the four |c| = 1 populations (momentum unchanged), then the rest
+  // population restores mass.
+  const float fix = 0.25f * (target_e - moved_e);
+#pragma unroll
+  for (int l = 1; l <= 4; ++l) d[l] += fix;
+  d[0] -= moved + 4.0f * fix;
+}
+
+// Halo images as in the FP64 store_site.
+__device__ __forceinline__ void store_site32(float* __restrict__ dst, const StepParams& p, int x, int y,
+                                             const float (&d)[kQ]) {
+  int xs[3] = {x, 0, 0}, ys[3] = {y, 0, 0};
+  int nx = 1, ny = 1;
+  if (x < kHx) xs[nx++] = x + p.Lx;
+  if (x >= p.Lx - kHx) xs[nx++] = x - p.Lx;
+  if (p.periodic_y) {
+    if (y < kHx) ys[ny++] = y + p.Ly;
+    if (y >= p.Ly - kHx) ys[ny++] = y - p.Ly;
+  }
+  for (int a = 0; a < nx; ++a)
+    for (int b = 0; b < ny; ++b) {
+      const int i = (int)site_index(p, xs[a], ys[b]);  // a plane holds < 2^31 elements
+#pragma unroll
+      for (int l = 0; l < kQ; ++l) (dst + l * p.plane)[i] = d[l];
+    }
+}
+
+// Wall bc in deviation form (rows 0..2 from each wall): the outgoing mass
+// sum (w_l + d_l) over the leaving (row, population) pairs of the column, and
+// missing d_l = rho_w f^eq_l(1, 0, T_wall) - w_l; FP64 (wall bands only).
+__device__ __forceinline__ double wall_density32(const float* __restrict__ src, const StepParams& p, int x,
+                                                 int wall) {
+  double out = 0.0;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int y = wall ? p.Ly - 1 - r : r;
+    const long long i = site_index(p, x, y);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const int cy = vel_cy(l);
+      if (wall ? (cy > r) : (cy < -r)) out += (double)c_shell32.w[vel_shell(l)] + (double)src[l * p.plane + i];
+    }
+  }
+  return out * p.inv_denom[wall];
+}
+
+__device__ __forceinline__ float missing32(const StepParams& p, double rho_w, int wall, int l) {
+  return (float)(rho_w * p.fw[wall][l] - c_shell32.w64[vel_shell(l)]);
+}
+
+__global__ void __launch_bounds__(256) wrap32_kernel(float* __restrict__ buf, StepParams p) {
+  const int rows_a = p.periodic_y ? p.Ly + 2 * kHx : p.Ly;
+  const int y0 = p.periodic_y ? -kHx : 0;
+  const long long n_a = (long long)kQ * 6 * rows_a;
+  const long long n_b = p.periodic_y ? (long long)kQ * p.Lx * 6 : 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n_a + n_b;
+       t += (long long)gridDim.x * blockDim.x) {
+    int l, xd, yd, xs, ys;
+    if (t < n_a) {
+      const int yy = (int)(t % rows_a);
+      const int h = (int)((t / rows_a) % 6);
+      l = (int)(t / (6LL * rows_a));
+      xd = h < 3 ? h - 3 : p.Lx + h - 3;
+      xs = h < 3 ? p.Lx + h - 3 : h - 3;
+      yd = y0 + yy;
+      ys = yd < 0 ? yd + p.Ly : (yd >= p.Ly ? yd - p.Ly : yd);
+    } else {
+      const long long u = t - n_a;
+      const int r = (int)(u % 6);
+      xd = (int)((u / 6) % p.Lx);
+      l = (int)(u / (6LL * p.Lx));
+      xs = xd;
+      yd = r < 3 ? r - 3 : p.Ly + r - 3;
+      ys = r < 3 ? p.Ly + r - 3 : r - 3;
+    }
+    buf[l * p.plane + site_index(p, xd, yd)] = buf[l * p.plane + site_index(p, xs, ys)];
+  }
+}
+
+// One site of the fused step (pull, wall bc on the wall bands, collide,
+// store with halo images).
+template <class W>
+__device__ __forceinline__ void fused_site32(const float* __restrict__ src, float* __restrict__ dst,
+                                             const StepParams& p, int x, int y) {
+  // 64-bit plane base (uniform across the block) plus a 32-bit offset
+  const int i = (int)site_index(p, x, y);
+  float d[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) d[l] = (src + l * p.plane)[i - vel_cx(l) * p.NY - vel_cy(l)];
+  if (!p.periodic_y && (y < 3 || y >= p.Ly - 3)) {
+    const int wall = y >= p.Ly - 3;
+    const int r = wall ? p.Ly - 1 - y : y;
+    const double rho_w = wall_density32(src, p, x, wall);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const int cy = vel_cy(l);
+      if (wall ? (cy < -r) : (cy > r)) d[l] = missing32(p, rho_w, wall, l);
+    }
+  }
+  collide_site32<W>(d, p);
+  store_site32(dst, p, x, y, d);
+}
+
+template <class W>
+__global__ void __launch_bounds__(kBlockY, D2Q37_FP32_MIN_BLOCKS) fused32_kernel(const float* __restrict__ src,
+                                                                                 float* __restrict__ dst,
+                                                                                 StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  fused_site32<W>(src, dst, p, x, y);
+}
+
+// Many lattices in one launch (see batch_fused_kernel of the FP64 kernels).
+template <class W, int BY>
+__global__ void __launch_bounds__(BY, (D2Q37_FP32_MIN_BLOCKS * 128) / BY) batch_fused32_kernel(
+    const BatchEntry* __restrict__ tab, int n, long long tiles, int parity) {
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const BatchEntry& e = tab[batch_entry_of(tab, n, t)];
+    const long long local = t - e.tile0;
+    const int x = (int)(local / e.ytiles);
+    const int y = (int)(local - (long long)x * e.ytiles) * BY + threadIdx.x;
+    const int c = e.cur ^ parity;
+    if (y < e.p.Ly) fused_site32<W>((const float*)e.buf[c], (float*)e.buf[c ^ 1], e.p, x, y);
+  }
+}
+
+__global__ void __launch_bounds__(kBlockY) propagate32_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                                              StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  const long long i = site_index(p, x, y);
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) dst[l * p.plane + i] = src[l * p.plane + i - vel_cx(l) * p.NY - vel_cy(l)];
+}
+
+__global__ void __launch_bounds__(128) bc32_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                                   StepParams p) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * p.Lx) return;
+  const int wall = t >= p.Lx;
+  const int x = t - wall * p.Lx;
+  const double rho_w = wall_density32(src, p, x, wall);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int y = wall ? p.Ly - 1 - r : r;
+    const long long i = site_index(p, x, y);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      const int cy = vel_cy(l);
+      if (wall ? (cy < -r) : (cy > r)) dst[l * p.plane + i] = missing32(p, rho_w, wall, l);
+    }
+  }
+}
+
+template <class W>
+__global__ void __launch_bounds__(kBlockY, D2Q37_FP32_MIN_BLOCKS) collide32_kernel(float* __restrict__ buf,
+                                                                                   StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  const long long i = site_index(p, x, y);
+  float d[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) d[l] = buf[l * p.plane + i];
+  collide_site32<W>(d, p);
+  store_site32(buf, p, x, y, d);
+}
+
+// Fields in FP64 from the stored deviations.
+__global__ void __launch_bounds__(kBlockY) fields32_kernel(const float* __restrict__ buf, double* __restrict__ rho,
+                                                           double* __restrict__ u, double* __restrict__ T,
+                                                           StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  const long long i = site_index(p, x, y);
+  float d[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) d[l] = buf[l * p.plane + i];
+  const SiteScalars<WideF64> sc = site_scalars<WideF64>(d);
+  const long long o = (long long)x * p.Ly + y;
+  const long long n = (long long)p.Lx * p.Ly;
+  rho[o] = sc.rho;
+  u[o] = sc.ux;
+  u[n + o] = sc.uy;
+  T[o] = sc.T;
+}
+
+__global__ void __launch_bounds__(kBlockY) plane_to_frame32_kernel(float* __restrict__ frame,
+                                                                   const double* __restrict__ plane, int l,
+                                                                   StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  frame[l * p.plane + site_index(p, x, y)] =
+      (float)(plane[(long long)x * p.Ly + y] - c_shell32.w64[vel_shell(l)]);
+}
+
+__global__ void __launch_bounds__(kBlockY) frame32_to_plane_kernel(double* __restrict__ plane,
+                                                                   const float* __restrict__ frame, int l,
+                                                                   StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  plane[(long long)x * p.Ly + y] = c_shell32.w64[vel_shell(l)] + (double)frame[l * p.plane + site_index(p, x, y)];
+}
+
+dim3 site_grid(const StepParams& p) { return dim3(p.Lx, (p.Ly + kBlockY - 1) / kBlockY); }
+
+int done(int n) { return cudaGetLastError() == cudaSuccess ? n : -1; }
+
+}  // namespace
+
+int launch_plane_to_frame32(float* frame, const double* plane, int l, const StepParams& p, cudaStream_t stream) {
+  plane_to_frame32_kernel<<<site_grid(p), kBlockY, 0, stream>>>(frame, plane, l, p);
+  return done(1);
+}
+
+int launch_frame32_to_plane(double* plane, const float* frame, int l, const StepParams& p, cudaStream_t stream) {
+  frame32_to_plane_kernel<<<site_grid(p), kBlockY, 0, stream>>>(plane, frame, l, p);
+  return done(1);
+}
+
+cudaError_t upload_shell_consts32(const ShellConsts32& c) { return cudaMemcpyToSymbol(c_shell32, &c, sizeof(c)); }
+
+int launch_wrap32(float* buf, const StepParams& p, cudaStream_t stream) {
+  const long long n = (long long)kQ * 6 * (p.periodic_y ? p.Ly + 2 * kHx : p.Ly) +
+                      (p.periodic_y ? (long long)kQ * p.Lx * 6 : 0);
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  wrap32_kernel<<<(unsigned)blocks, 256, 0, stream>>>(buf, p);
+  return done(1);
+}
+
+int launch_propagate32(const float* src, float* dst, const StepParams& p, cudaStream_t stream) {
+  propagate32_kernel<<<site_grid(p), kBlockY, 0, stream>>>(src, dst, p);
+  return done(1);
+}
+
+int launch_bc32(const float* src, float* dst, const StepParams& p, cudaStream_t stream) {
+  bc32_kernel<<<(2 * p.Lx + 127) / 128, 128, 0, stream>>>(src, dst, p);
+  return done(1);
+}
+
+int launch_collide32(float* buf, const StepParams& p, bool wide_fp64, cudaStream_t stream) {
+  if (wide_fp64)
+    collide32_kernel<WideF64><<<site_grid(p), kBlockY, 0, stream>>>(buf, p);
+  else
+    collide32_kernel<WideDF><<<site_grid(p), kBlockY, 0, stream>>>(buf, p);
+  return done(1);
+}
+
+int launch_fused32(const float* src, float* dst, const StepParams& p, bool wide_fp64, cudaStream_t stream) {
+  if (wide_fp64)
+    fused32_kernel<WideF64><<<site_grid(p), kBlockY, 0, stream>>>(src, dst, p);
+  else
+    fused32_kernel<WideDF><<<site_grid(p), kBlockY, 0, stream>>>(src, dst, p);
+  return done(1);
+}
+
+template <class W, int BY>
+int batch32_launch(const BatchEntry* tab, int n, long long tiles, int parity, int grid, cudaStream_t stream) {
+  batch_fused32_kernel<W, BY><<<grid, BY, 0, stream>>>(tab, n, tiles, parity);
+  return done(1);
+}
+
+template <class W, int BY>
+int batch32_occupancy() {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_fused32_kernel<W, BY>, BY, 0);
+  return b;
+}
+
+int launch_batch_fused32(const BatchEntry* tab, int n, long long tiles, int parity, int block_y, int grid,
+                         bool wide_fp64, cudaStream_t stream) {
+  switch (block_y) {
+    case 64: return wide_fp64 ? batch32_launch<WideF64, 64>(tab, n, tiles, parity, grid, stream)
+                              : batch32_launch<WideDF, 64>(tab, n, tiles, parity, grid, stream);
+    case 128: return wide_fp64 ? batch32_launch<WideF64, 128>(tab, n, tiles, parity, grid, stream)
+                               : batch32_launch<WideDF, 128>(tab, n, tiles, parity, grid, stream);
+    case 256: return wide_fp64 ? batch32_launch<WideF64, 256>(tab, n, tiles, parity, grid, stream)
+                               : batch32_launch<WideDF, 256>(tab, n, tiles, parity, grid, stream);
+    default: return -1;
+  }
+}
+
+int batch32_blocks_per_sm(int block_y, bool wide_fp64) {
+  switch (block_y) {
+    case 64: return wide_fp64 ? batch32_occupancy<WideF64, 64>() : batch32_occupancy<WideDF, 64>();
+    case 128: return wide_fp64 ? batch32_occupancy<WideF64, 128>() : batch32_occupancy<WideDF, 128>();
+    case 256: return wide_fp64 ? batch32_occupancy<WideF64, 256>() : batch32_occupancy<WideDF, 256>();
+    default: return 0;
+  }
+}
+
+int launch_fields32(const float* buf, double* rho, double* u, double* T, const StepParams& p, cudaStream_t stream) {
+  fields32_kernel<<<site_grid(p), kBlockY, 0, stream>>>(buf, rho, u, T, p);
+  return done(1);
+}
+
+}  // namespace d2q37

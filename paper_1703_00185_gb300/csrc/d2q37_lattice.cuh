@@ -106,8 +106,8 @@ constexpr int kHy32 = 32;
 // Quadrature constants for the FP32-storage kernels: the wide-precision ones
 // as FP64 and as double-float (hi, lo) pairs, the rest in FP32.
 struct ShellConsts32 {
-  double s, s2;
-  float s_hi, s_lo, s2_hi, s2_lo;
+  double s, s2, inv_s2;
+  float s_hi, s_lo, s2_hi, s2_lo, inv_s2_hi, inv_s2_lo;
   double x2[kShells];  // s^2 |c|^2 per shell
   float x2_hi[kShells], x2_lo[kShells];
   double w64[kShells];
@@ -132,6 +132,29 @@ struct StepParams {
   double fw[2][kQ];   // wall equilibria f^eq(1, 0, T_wall): [0] bottom, [1] top
   double inv_denom[2];// 1 / sum of fw over the missing (row, population) pairs
 };
+
+// One lattice of a batched launch.  Tiles are one column x by `block_y`
+// consecutive rows; this lattice owns tiles [tile0, tile0 + Lx * ytiles).
+struct BatchEntry {
+  StepParams p;
+  void* buf[2];
+  int cur;          // buffer holding the state when the launch parity is 0
+  int ytiles;       // ceil(Ly / block_y)
+  long long tile0;  // first tile of this lattice
+};
+
+// Index of the entry owning tile t (entries sorted by tile0, tile0[0] = 0).
+__device__ __forceinline__ int batch_entry_of(const BatchEntry* __restrict__ tab, int n, long long t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].tile0 <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
 
 // f^eq of one site into feq[37] (host or device).
 __host__ __device__ inline void equilibrium(const ShellConsts& c, double rho, double ux, double uy, double T,

@@ -30,5 +30,19 @@ int launch_collide32(float* buf, const StepParams& p, bool wide_fp64, cudaStream
 int launch_fused32(const float* src, float* dst, const StepParams& p, bool wide_fp64, cudaStream_t stream);
 int launch_fields32(const float* buf, double* rho, double* u, double* T, const StepParams& p, cudaStream_t stream);
 int launch_init_equilibrium32(float* buf, const double* T, const StepParams& p, cudaStream_t stream);
+// Batched fused step over a table of n lattices (BatchEntry, device memory),
+// tiles of block_y rows; block_y in {64, 128, 256}; grid = number of blocks
+// of the grid-stride loop.  *_blocks_per_sm: resident blocks per SM.
+int launch_batch_fused(const BatchEntry* tab, int n, long long tiles, int parity, int block_y, int grid,
+                       cudaStream_t stream);
+int batch_blocks_per_sm(int block_y);
+int launch_batch_fused32(const BatchEntry* tab, int n, long long tiles, int parity, int block_y, int grid,
+                         bool wide_fp64, cudaStream_t stream);
+int batch32_blocks_per_sm(int block_y, bool wide_fp64);
+
+// One population plane between a contiguous FP64 [Lx][Ly] array (f) and the
+// FP32 deviation frame (d = f - w_l).
+int launch_plane_to_frame32(float* frame, const double* plane, int l, const StepParams& p, cudaStream_t stream);
+int launch_frame32_to_plane(double* plane, const float* frame, int l, const StepParams& p, cudaStream_t stream);
 
 }  // namespace d2q37

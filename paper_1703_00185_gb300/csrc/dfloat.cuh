@@ -1,0 +1,106 @@
+// Double-float ("df") arithmetic on the FP32 pipes: a value is the unevaluated
+// sum hi + lo of two floats with |lo| <= ulp(hi)/2, about 48 significant bits.
+//
+// GB300 runs FP32 at 64x its FP64 rate, so where a kernel needs more than
+// FP32 precision but not the full FP64 exponent range, df keeps the work on
+// the FP32 pipes.  Algorithms: Knuth's two-sum, Dekker's fast two-sum and the
+// fma-based exact product, composed as in Hida, Li & Bailey's QD library
+// ("accurate" addition).  Every operation uses the _rn intrinsics so the
+// compiler cannot contract or reassociate them.
+#pragma once
+
+#include <cstdint>
+
+namespace d2q37 {
+
+struct dfloat {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dfloat df_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ dfloat df(float a) { return {a, 0.0f}; }
+
+__device__ __forceinline__ dfloat df_neg(dfloat x) { return {-x.hi, -x.lo}; }
+
+__device__ __forceinline__ dfloat df_add(dfloat x, dfloat y) {
+  dfloat s = df_two_sum(x.hi, y.hi);
+  const dfloat t = df_two_sum(x.lo, y.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = df_fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ dfloat df_sub(dfloat x, dfloat y) { return df_add(x, df_neg(y)); }
+
+// "Sloppy" addition (one two-sum instead of two): relative error about
+// 2^-44 even when the low parts cancel, 11 FP32 operations instead of 20.
+__device__ __forceinline__ dfloat df_add_fast(dfloat x, dfloat y) {
+  dfloat s = df_two_sum(x.hi, y.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ dfloat df_add(dfloat x, float y) {
+  dfloat s = df_two_sum(x.hi, y);
+  s.lo = __fadd_rn(s.lo, x.lo);
+  return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ dfloat df_mul(dfloat x, dfloat y) {
+  dfloat p = df_two_prod(x.hi, y.hi);
+  p.lo = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
+  return df_fast_two_sum(p.hi, p.lo);
+}
+
+__device__ __forceinline__ dfloat df_mul(dfloat x, float y) {
+  dfloat p = df_two_prod(x.hi, y);
+  p.lo = __fmaf_rn(x.lo, y, p.lo);
+  return df_fast_two_sum(p.hi, p.lo);
+}
+
+// x * y + z
+__device__ __forceinline__ dfloat df_fma(dfloat x, dfloat y, dfloat z) { return df_add(df_mul(x, y), z); }
+
+// 1 / y: float seed refined by one Newton step in df (error ~ 2^-46 relative).
+__device__ __forceinline__ dfloat df_rcp(dfloat y) {
+  const float r = __frcp_rn(y.hi);
+  const dfloat e = df_add(df(1.0f), df_neg(df_mul(y, r)));  // 1 - y r
+  return df_add(df(r), df_mul(e, r));                       // r + r (1 - y r)
+}
+
+__device__ __forceinline__ float df_to_float(dfloat x) { return __fadd_rn(x.hi, x.lo); }
+
+// Exact-ish conversion of a 64-bit integer scaled by 2^scale_exp: the value
+// is split into 24-bit pieces (each exact in FP32) and summed in df.
+__device__ __forceinline__ dfloat df_from_int64(long long v, int scale_exp) {
+  const bool neg = v < 0;
+  const unsigned long long m = neg ? (unsigned long long)(-v) : (unsigned long long)v;
+  const float a = (float)(unsigned)(m >> 48);               // bits 48..63 (< 2^16)
+  const float b = (float)(unsigned)((m >> 24) & 0xFFFFFF);  // bits 24..47
+  const float c = (float)(unsigned)(m & 0xFFFFFF);          // bits 0..23
+  dfloat r = df_two_sum(__fmul_rn(a, 281474976710656.0f), __fmul_rn(b, 16777216.0f));
+  r = df_add(r, c);
+  const float s = __int_as_float((scale_exp + 127) << 23);  // 2^scale_exp, scale_exp in [-126, 127]
+  r.hi = __fmul_rn(r.hi, s);
+  r.lo = __fmul_rn(r.lo, s);
+  return neg ? df_neg(r) : r;
+}
+
+}  // namespace d2q37
