@@ -51,6 +51,13 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "fp32", "fp32-df"], default="fp64")
     ap.add_argument("--no-precision-forms", dest="precision_forms", action="store_false",
                     help="skip timing the FP32-storage forms after the FP64 step")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip timing the 64-lattice batched forms")
+    ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--serving-jobs", type=int, default=40, help="0 skips the serving run")
+    ap.add_argument("--serving-budget-gb", type=float, default=96.0)
+    ap.add_argument("--serving-steps-per-tick", type=int, default=16)
+    ap.add_argument("--serving-time-limit", type=float, default=90.0)
     ap.add_argument("--accuracy-steps", type=int, default=100,
                     help="steps after which the FP32-storage forms are compared with the FP64 step")
     ap.add_argument("--Lx", type=int, default=2048)
@@ -242,6 +249,64 @@ def time_form(torch, lbm, a, dev, precision, kernel, steps, seed, dist=None, sam
     return lat, ms, launches, kt, clocks
 
 
+def run_batched(torch, lbm, a, dev):
+    """64 uneven Rayleigh-Taylor lattices advanced together, one launch per
+    step (graph-replayed), launch shape from the autotuner; FP64 and FP32."""
+    from paper_1703_00185_gb300 import workloads
+    jobs = workloads.batched_lattices(1, 64)
+    sites = sum(j["Lx"] * j["Ly"] for j in jobs)
+    out = {"workload": "64 Rayleigh-Taylor lattices, Lx in {128..1024 step 128}, Ly in {256..2048 step 256}, "
+                       "per-lattice seed and T_bot ~ U(1.2, 1.8) from master seed 1", "sites": sites}
+    for prec in ("fp64", "fp32-df"):
+        lats = []
+        for j in jobs:
+            lat = lbm.Lattice(j["Lx"], j["Ly"], tau=0.8, g0=1e-4, T_top=0.5, T_bot=j["T_bot"], device=dev,
+                              precision=prec)
+            lat.init_rayleigh_taylor(j["seed"])
+            lats.append(lat)
+        b = lbm.Batch(lats)
+        tune = b.autotune(trial_steps=3, use_cache=False)
+        b.step(a.warmup)
+        b.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = b.launch_count
+        e0.record(b.stream)
+        b.step(a.batched_steps)
+        e1.record(b.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[prec] = {"value": round(sites * a.batched_steps / (ms * 1e-3) / 1e6, 3), "unit": UNIT,
+                     "ms_per_step": round(ms / a.batched_steps, 4), "steps": a.batched_steps,
+                     "gpu_launches": b.launch_count - n0, "launch_shape": tune,
+                     "hbm_frac": round(BYTES_PER_SITE[prec] * sites * a.batched_steps / (ms * 1e-3) / 1e9 /
+                                       measured_peaks().get("hbm_gbs", float("nan")), 4)}
+        b.close()
+        for lat in lats:
+            lat.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_serving(a, dev):
+    """The serving form: a finite Poisson trace at the configured rate (the
+    first `serving_jobs` arrivals), plus lower rates on jobs of 1/4 the linear
+    size, replayed in wall-clock time through the continuous-batching server."""
+    from paper_1703_00185_gb300 import serving, workloads
+    budget = int(a.serving_budget_gb * 2 ** 30)
+    runs = {}
+    trace = workloads.serving_trace(1, rate=50.0, n_jobs=a.serving_jobs)
+    runs["rate50_full_size"] = serving.run_trace(trace, budget, a.serving_steps_per_tick, dev,
+                                                 time_limit=a.serving_time_limit)
+    for rate in (20.0, 5.0):
+        trace = workloads.serving_trace(2, rate=rate, n_jobs=a.serving_jobs, size_scale=0.25)
+        runs["rate%g_quarter_size" % rate] = serving.run_trace(trace, budget, a.serving_steps_per_tick, dev,
+                                                               time_limit=a.serving_time_limit)
+    return {"workload": "Poisson arrivals (seeded), Lx log-uniform [64, 2048], Ly log-uniform [64, 4096] "
+                        "(multiples of 8; quarter-size runs divide both by 4), steps U(100, 5000), precision "
+                        "50/50 FP64 or FP32 storage (double-float wide terms)",
+            "budget_gb": a.serving_budget_gb, "max_steps_per_tick": a.serving_steps_per_tick, "runs": runs}
+
+
 def run_ours(a):
     rank, local_rank, world = dist_env()
     cpu = None
@@ -316,6 +381,8 @@ def run_ours(a):
                            "rel_l2_vs_fp64_after_%d_steps" % a.accuracy_steps:
                                {"rho": errs[0], "u": errs[1], "T": errs[2]},
                            "gpu_launches": fl}
+    batched = run_batched(torch, lbm, a, dev) if (a.batched and a.precision == "fp64") else None
+    serving_summary = run_serving(a, dev) if (a.serving_jobs > 0 and a.precision == "fp64") else None
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
@@ -328,7 +395,7 @@ def run_ours(a):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "kernel_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]}, "clocks": clocks,
-                "precision_forms": forms or None}
+                "precision_forms": forms or None, "batched_forms": batched, "serving": serving_summary}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

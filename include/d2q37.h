@@ -203,6 +203,59 @@ int64_t lbm_batch_launch_count(const lbm_batch_t* b);
 /* Release the batch (not its lattices).  NULL-safe. */
 void lbm_batch_destroy(lbm_batch_t* b);
 
+/* ---- serving: continuous batching of simulation jobs ----------------------
+ * Not in the paper.  A job is a Rayleigh-Taylor lattice (size, parameters,
+ * precision, seed) to advance a given number of steps.  Jobs queue on
+ * submission and are admitted, in arrival order with later jobs allowed to
+ * pass ones that do not fit yet, whenever their device memory
+ * (lbm_required_bytes) fits in the free part of one pre-allocated pool of
+ * hbm_budget_bytes.  Each lbm_server_tick admits what fits, advances every
+ * admitted job by k = min(max_steps_per_tick, fewest steps left) steps with
+ * one batched fused launch per step and precision group (each group on its
+ * own stream, so their work overlaps), then copies the fields of jobs that
+ * reached their step count to host memory and frees their device memory.
+ * All calls are from one host thread; a tick synchronises its streams. */
+typedef struct lbm_server_t lbm_server_t;
+
+#define LBM_JOB_QUEUED 0
+#define LBM_JOB_ACTIVE 1
+#define LBM_JOB_DONE 2
+
+typedef struct {
+  int64_t submitted, completed, queued, active;
+  int64_t ticks, steps, launches; /* ticks run, steps advanced, kernels launched */
+  size_t budget_bytes, bytes_in_use, largest_free_bytes;
+} lbm_server_stats;
+
+/* Allocates the pool (cudaMalloc of hbm_budget_bytes) and 3 streams on the
+ * current device.  LBM_ENOMEM if the pool cannot be allocated. */
+int lbm_server_create(size_t hbm_budget_bytes, int max_steps_per_tick, lbm_server_t** out);
+
+/* Queue a job; *job_id receives its id (> 0).  p->kernel is ignored (fused).
+ * LBM_EINVAL for invalid sizes or parameters, LBM_ENOMEM if the job alone
+ * exceeds the budget. */
+int lbm_server_submit(lbm_server_t* s, int Lx, int Ly, int steps, const lbm_params* p, uint64_t seed,
+                      int64_t* job_id);
+
+/* One scheduling round (see above); *steps_done (may be NULL) = k, 0 when no
+ * job is active. */
+int lbm_server_tick(lbm_server_t* s, int* steps_done);
+
+/* Ids of jobs completed since the last poll (at most max_ids); *n = count. */
+int lbm_server_poll(lbm_server_t* s, int64_t* ids, int max_ids, int* n);
+
+/* State (LBM_JOB_*) and steps left of a job that has not been fetched. */
+int lbm_server_job_state(const lbm_server_t* s, int64_t id, int* state, int* steps_left);
+
+/* Copy a completed job's fields (layout of lbm_fields) and forget the job.
+ * LBM_ESTATE if it has not completed. */
+int lbm_server_fetch(lbm_server_t* s, int64_t id, double* rho, double* u, double* T);
+
+int lbm_server_stats_get(const lbm_server_t* s, lbm_server_stats* out);
+
+/* Release the pool, streams and every job.  NULL-safe. */
+void lbm_server_destroy(lbm_server_t* s);
+
 const char* lbm_strerror(int code);
 
 #ifdef __cplusplus

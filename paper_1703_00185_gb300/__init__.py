@@ -29,6 +29,16 @@ class LBMError(RuntimeError):
         super().__init__("%s failed: %s (%d)" % (what, lbm_strerror(code) if _lib else "library error", code))
 
 
+class lbm_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("active", ctypes.c_int64), ("ticks", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("budget_bytes", ctypes.c_size_t), ("bytes_in_use", ctypes.c_size_t),
+                ("largest_free_bytes", ctypes.c_size_t)]
+
+
+JOB_QUEUED, JOB_ACTIVE, JOB_DONE = 0, 1, 2
+
+
 class lbm_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("g0", ctypes.c_double), ("T_top", ctypes.c_double),
                 ("T_bot", ctypes.c_double), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
@@ -76,6 +86,15 @@ def load_library():
         "lbm_batch_synchronize": (ctypes.c_int, [vp]),
         "lbm_batch_launch_count": (ctypes.c_int64, [vp]),
         "lbm_batch_destroy": (None, [vp]),
+        "lbm_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]),
+        "lbm_server_submit": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, ctypes.c_uint64,
+                                             ctypes.POINTER(ctypes.c_int64)]),
+        "lbm_server_tick": (ctypes.c_int, [vp, ip]),
+        "lbm_server_poll": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ip]),
+        "lbm_server_job_state": (ctypes.c_int, [vp, ctypes.c_int64, ip, ip]),
+        "lbm_server_fetch": (ctypes.c_int, [vp, ctypes.c_int64, vp, vp, vp]),
+        "lbm_server_stats_get": (ctypes.c_int, [vp, ctypes.POINTER(lbm_server_stats)]),
+        "lbm_server_destroy": (None, [vp]),
         "lbm_destroy": (None, [vp]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     }
@@ -94,7 +113,9 @@ def exported_symbols():
             "lbm_step", "lbm_run_phases", "lbm_fields", "lbm_fields_device", "lbm_synchronize",
             "lbm_launch_count", "lbm_set_timing", "lbm_kernel_times", "lbm_destroy", "lbm_strerror",
             "lbm_batch_create", "lbm_batch_step", "lbm_batch_set_config", "lbm_batch_get_config",
-            "lbm_batch_autotune", "lbm_batch_synchronize", "lbm_batch_launch_count", "lbm_batch_destroy"]
+            "lbm_batch_autotune", "lbm_batch_synchronize", "lbm_batch_launch_count", "lbm_batch_destroy",
+            "lbm_server_create", "lbm_server_submit", "lbm_server_tick", "lbm_server_poll", "lbm_server_job_state",
+            "lbm_server_fetch", "lbm_server_stats_get", "lbm_server_destroy"]
 
 
 KERNEL_KINDS = ("wrap", "propagate", "bc", "collide", "fused", "fields", "init", "convert")

@@ -341,8 +341,10 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(c
 template <int BY>
 __global__ void __launch_bounds__(BY, (D2Q37_SITE_MIN_BLOCKS * 128) / BY) batch_fused_kernel(
     const BatchEntry* __restrict__ tab, int n, long long tiles, int parity) {
+  __shared__ BatchEntry se;
+  int cached = -1;
   for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const BatchEntry& e = tab[batch_entry_of(tab, n, t)];
+    const BatchEntry& e = batch_entry_shared<BY>(tab, n, t, se, cached);
     const long long local = t - e.tile0;
     const int x = (int)(local / e.ytiles);
     const int y = (int)(local - (long long)x * e.ytiles) * BY + threadIdx.x;

@@ -1,0 +1,366 @@
+// Simulation server with continuous batching (C ABI lbm_server_*, declared
+// in include/d2q37.h).
+//
+// Jobs (lattice size, step count, parameters, precision, seed) are queued on
+// submission and admitted in arrival order, skipping ahead to any later job
+// that fits, whenever their device memory fits in the free part of one
+// pre-allocated pool (the HBM budget; first-fit with coalescing).  Admitted
+// jobs keep their state on the device.  Each tick advances every active job
+// by k steps, k = min(steps per tick, fewest steps left), with one batched
+// fused launch per step for each precision group; the groups run on their own
+// streams so their work overlaps.  A job that reaches its step count has its
+// fields copied to host memory and its device memory returned to the pool;
+// the next tick can admit queued jobs into it.
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "d2q37_handle.h"
+
+namespace {
+
+constexpr int kGroups = 3;  // one per storage precision
+
+struct Job {
+  int64_t id;
+  int Lx, Ly, steps_total, steps_left;
+  lbm_params prm;
+  uint64_t seed;
+  int state;  // LBM_JOB_*
+  size_t bytes, offset;
+  lbm_t* h;
+  std::vector<double> rho, u, T;  // results once done
+};
+
+// First-fit allocator over [0, size) with coalescing of freed ranges.
+class Pool {
+ public:
+  void reset(size_t size) {
+    free_.clear();
+    if (size) free_[0] = size;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const size_t rest = it->second - bytes;
+      const size_t start = it->first + bytes;
+      free_.erase(it);
+      if (rest) free_[start] = rest;
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    auto it = free_.emplace(off, bytes).first;
+    auto next = std::next(it);
+    if (next != free_.end() && it->first + it->second == next->first) {
+      it->second += next->second;
+      free_.erase(next);
+    }
+    if (it != free_.begin()) {
+      auto prev = std::prev(it);
+      if (prev->first + prev->second == it->first) {
+        prev->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t largest() const {
+    size_t m = 0;
+    for (const auto& kv : free_) m = std::max(m, kv.second);
+    return m;
+  }
+
+ private:
+  std::map<size_t, size_t> free_;
+};
+
+size_t round256(size_t n) { return (n + 255) & ~size_t(255); }
+
+int group_of(int precision) { return precision; }  // LBM_PRECISION_* are 0, 1, 2
+
+}  // namespace
+
+struct lbm_server_t {
+  size_t budget, in_use;
+  char* pool_mem;
+  Pool pool;
+  int max_steps_per_tick;
+  int64_t next_id;
+  std::deque<Job*> queue;
+  std::vector<Job*> active;
+  std::unordered_map<int64_t, Job*> jobs;
+  std::vector<int64_t> finished;  // not yet reported by lbm_server_poll
+  cudaStream_t stream[kGroups];
+  BatchEntry* dev_tab[kGroups];
+  int dev_cap[kGroups];
+  bool dirty;
+  int sms;
+  lbm_server_stats stats;
+};
+
+namespace {
+
+void release_job_memory(lbm_server_t* s, Job* j) {
+  if (j->h) {
+    lbm_destroy(j->h);
+    j->h = nullptr;
+  }
+  if (j->bytes) {
+    s->pool.release(j->offset, j->bytes);
+    s->in_use -= j->bytes;
+    j->bytes = 0;
+  }
+}
+
+// Admit queued jobs in arrival order while memory allows (skipping jobs that
+// do not fit yet).
+int admit(lbm_server_t* s) {
+  for (auto it = s->queue.begin(); it != s->queue.end();) {
+    Job* j = *it;
+    const size_t need = round256(lbm_required_bytes(j->Lx, j->Ly, &j->prm));
+    size_t off = 0;
+    if (!s->pool.alloc(need, &off)) {
+      ++it;
+      continue;
+    }
+    j->offset = off;
+    j->bytes = need;
+    s->in_use += need;
+    const int g = group_of(j->prm.precision);
+    int rc = lbm_create_ext(j->Lx, j->Ly, &j->prm, s->pool_mem + off, need, s->stream[g], &j->h);
+    if (!rc) rc = lbm_init_rayleigh_taylor(j->h, j->seed);
+    if (!rc) rc = handle_prepare_halos(j->h, s->stream[g]);
+    if (rc) {
+      release_job_memory(s, j);
+      return rc;
+    }
+    j->state = LBM_JOB_ACTIVE;
+    s->active.push_back(j);
+    s->dirty = true;
+    it = s->queue.erase(it);
+  }
+  return LBM_OK;
+}
+
+// Rebuild and upload each group's tile table (tiles of 128 rows).
+int rebuild_tables(lbm_server_t* s, std::vector<BatchEntry> (&tab)[kGroups], long long (&tiles)[kGroups]) {
+  for (int g = 0; g < kGroups; ++g) {
+    tab[g].clear();
+    tiles[g] = 0;
+  }
+  for (Job* j : s->active) {
+    const int g = group_of(j->prm.precision);
+    BatchEntry e;
+    std::memset(&e, 0, sizeof(e));
+    e.p = j->h->sp;
+    e.buf[0] = j->h->buf[0];
+    e.buf[1] = j->h->buf[1];
+    e.cur = j->h->cur;
+    e.ytiles = (j->Ly + 127) / 128;
+    e.tile0 = tiles[g];
+    tiles[g] += (long long)j->Lx * e.ytiles;
+    tab[g].push_back(e);
+  }
+  for (int g = 0; g < kGroups; ++g) {
+    const int n = (int)tab[g].size();
+    if (!n) continue;
+    if (n > s->dev_cap[g]) {
+      if (s->dev_tab[g]) cudaFree(s->dev_tab[g]);
+      s->dev_tab[g] = nullptr;
+      const int cap = std::max(n, 2 * s->dev_cap[g]);
+      if (cudaMalloc(&s->dev_tab[g], cap * sizeof(BatchEntry)) != cudaSuccess) {
+        cudaGetLastError();
+        s->dev_cap[g] = 0;
+        return LBM_ENOMEM;
+      }
+      s->dev_cap[g] = cap;
+    }
+    if (cudaMemcpyAsync(s->dev_tab[g], tab[g].data(), n * sizeof(BatchEntry), cudaMemcpyHostToDevice,
+                        s->stream[g]) != cudaSuccess)
+      return LBM_ECUDA;
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_server_create(size_t hbm_budget_bytes, int max_steps_per_tick, lbm_server_t** out) {
+  if (!out || hbm_budget_bytes < 4096 || max_steps_per_tick <= 0) return LBM_EINVAL;
+  int rc = handle_device_consts();
+  if (rc) return rc;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return LBM_ECUDA;
+  lbm_server_t* s = new lbm_server_t();
+  s->budget = hbm_budget_bytes & ~size_t(255);
+  s->max_steps_per_tick = max_steps_per_tick;
+  s->sms = sms;
+  s->next_id = 1;
+  if (cudaMalloc(&s->pool_mem, s->budget) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return LBM_ENOMEM;
+  }
+  s->pool.reset(s->budget);
+  for (int g = 0; g < kGroups && !rc; ++g)
+    if (cudaStreamCreateWithFlags(&s->stream[g], cudaStreamNonBlocking) != cudaSuccess) rc = LBM_ECUDA;
+  if (rc) {
+    lbm_server_destroy(s);
+    return rc;
+  }
+  s->stats.budget_bytes = s->budget;
+  *out = s;
+  return LBM_OK;
+}
+
+int lbm_server_submit(lbm_server_t* s, int Lx, int Ly, int steps, const lbm_params* p, uint64_t seed,
+                      int64_t* job_id) {
+  if (!s || !p || steps < 0 || !job_id) return LBM_EINVAL;
+  const size_t need = lbm_required_bytes(Lx, Ly, p);
+  if (!need) return LBM_EINVAL;
+  if (round256(need) > s->budget) return LBM_ENOMEM;  // could never be admitted
+  Job* j = new Job();
+  j->id = s->next_id++;
+  j->Lx = Lx;
+  j->Ly = Ly;
+  j->steps_total = j->steps_left = steps;
+  j->prm = *p;
+  j->prm.kernel = LBM_KERNEL_FUSED;
+  j->seed = seed;
+  j->state = LBM_JOB_QUEUED;
+  s->jobs[j->id] = j;
+  s->queue.push_back(j);
+  s->stats.submitted++;
+  *job_id = j->id;
+  return LBM_OK;
+}
+
+int lbm_server_tick(lbm_server_t* s, int* steps_done) {
+  if (!s) return LBM_EINVAL;
+  if (steps_done) *steps_done = 0;
+  int rc = admit(s);
+  if (rc) return rc;
+  if (s->active.empty()) return LBM_OK;
+  int k = s->max_steps_per_tick;
+  for (Job* j : s->active) k = std::min(k, j->steps_left);
+  std::vector<BatchEntry> tab[kGroups];
+  long long tiles[kGroups];
+  // the tables are rebuilt every tick: cheap (one entry per job) and it
+  // picks up each job's current buffer
+  rc = rebuild_tables(s, tab, tiles);
+  if (rc) return rc;
+  for (int g = 0; g < kGroups; ++g) {
+    const int n = (int)tab[g].size();
+    if (!n || k == 0) continue;
+    const int grid = (int)std::min<long long>(tiles[g], 2147483647LL);
+    for (int t = 0; t < k; ++t) {
+      const int launched = g == LBM_PRECISION_FP64
+                               ? launch_batch_fused(s->dev_tab[g], n, tiles[g], t & 1, 128, grid, s->stream[g])
+                               : launch_batch_fused32(s->dev_tab[g], n, tiles[g], t & 1, 128, grid,
+                                                      g == LBM_PRECISION_FP32_FP64, s->stream[g]);
+      if (launched < 0) return LBM_ECUDA;
+      s->stats.launches += launched;
+    }
+  }
+  // completed jobs: fields into their scratch, then to host
+  std::vector<Job*> done;
+  for (Job* j : s->active) {
+    j->h->cur ^= (k & 1);
+    j->steps_left -= k;
+    if (j->steps_left == 0) done.push_back(j);
+  }
+  for (Job* j : done) {
+    const size_t n = (size_t)j->Lx * j->Ly;
+    j->rho.resize(n);
+    j->u.resize(2 * n);
+    j->T.resize(n);
+    rc = lbm_fields(j->h, j->rho.data(), j->u.data(), j->T.data());  // on the job's group stream, synchronising
+    if (rc) return rc;
+  }
+  for (int g = 0; g < kGroups; ++g)
+    if (cudaStreamSynchronize(s->stream[g]) != cudaSuccess) return LBM_ECUDA;
+  for (Job* j : done) {
+    release_job_memory(s, j);
+    j->state = LBM_JOB_DONE;
+    s->finished.push_back(j->id);
+    s->stats.completed++;
+  }
+  if (!done.empty())
+    s->active.erase(std::remove_if(s->active.begin(), s->active.end(),
+                                   [](Job* j) { return j->state == LBM_JOB_DONE; }),
+                    s->active.end());
+  s->stats.ticks++;
+  s->stats.steps += k;
+  if (steps_done) *steps_done = k;
+  return LBM_OK;
+}
+
+int lbm_server_poll(lbm_server_t* s, int64_t* ids, int max_ids, int* n) {
+  if (!s || !n || (max_ids > 0 && !ids)) return LBM_EINVAL;
+  const int m = std::min<int>(max_ids, (int)s->finished.size());
+  for (int i = 0; i < m; ++i) ids[i] = s->finished[i];
+  s->finished.erase(s->finished.begin(), s->finished.begin() + m);
+  *n = m;
+  return LBM_OK;
+}
+
+int lbm_server_job_state(const lbm_server_t* s, int64_t id, int* state, int* steps_left) {
+  if (!s || !state) return LBM_EINVAL;
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return LBM_EINVAL;
+  *state = it->second->state;
+  if (steps_left) *steps_left = it->second->steps_left;
+  return LBM_OK;
+}
+
+int lbm_server_fetch(lbm_server_t* s, int64_t id, double* rho, double* u, double* T) {
+  if (!s || !rho || !u || !T) return LBM_EINVAL;
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return LBM_EINVAL;
+  Job* j = it->second;
+  if (j->state != LBM_JOB_DONE) return LBM_ESTATE;
+  std::memcpy(rho, j->rho.data(), j->rho.size() * sizeof(double));
+  std::memcpy(u, j->u.data(), j->u.size() * sizeof(double));
+  std::memcpy(T, j->T.data(), j->T.size() * sizeof(double));
+  s->jobs.erase(it);
+  delete j;
+  return LBM_OK;
+}
+
+int lbm_server_stats_get(const lbm_server_t* s, lbm_server_stats* out) {
+  if (!s || !out) return LBM_EINVAL;
+  *out = s->stats;
+  out->queued = (int64_t)s->queue.size();
+  out->active = (int64_t)s->active.size();
+  out->bytes_in_use = s->in_use;
+  out->largest_free_bytes = s->pool.largest();
+  return LBM_OK;
+}
+
+void lbm_server_destroy(lbm_server_t* s) {
+  if (!s) return;
+  for (int g = 0; g < kGroups; ++g)
+    if (s->stream[g]) cudaStreamSynchronize(s->stream[g]);
+  for (auto& kv : s->jobs) {
+    if (kv.second->h) lbm_destroy(kv.second->h);
+    delete kv.second;
+  }
+  for (int g = 0; g < kGroups; ++g) {
+    if (s->dev_tab[g]) cudaFree(s->dev_tab[g]);
+    if (s->stream[g]) cudaStreamDestroy(s->stream[g]);
+  }
+  if (s->pool_mem) cudaFree(s->pool_mem);
+  delete s;
+}
+
+}  // extern "C"
