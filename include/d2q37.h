@@ -42,6 +42,7 @@ extern "C" {
 #define LBM_ECUDA (-3)    /* a CUDA call or kernel launch failed */
 #define LBM_ETIMEOUT (-4) /* reserved for bounded device waits */
 #define LBM_ESTATE (-5)   /* call out of order, e.g. a step before any initial state */
+#define LBM_ETOOBIG (-6)  /* more lattices than lbm_batch_step_static's fixed table holds */
 
 /* Phase bits for lbm_run_phases(). */
 #define LBM_PHASE_PROPAGATE 1 /* pbc + pull propagate (Sec. "Code Organization") */
@@ -202,6 +203,33 @@ int64_t lbm_batch_launch_count(const lbm_batch_t* b);
 
 /* Release the batch (not its lattices).  NULL-safe. */
 void lbm_batch_destroy(lbm_batch_t* b);
+
+/* ---- batched stepping without device allocation ----------------------------
+ * The paper has no counterpart; this exists for callers that cannot call
+ * cudaMalloc: programs whose device memory all belongs to a caching allocator
+ * or a pre-registered pool (an extra cudaMalloc would break their memory
+ * budget, or fail on a full device), and loops that cannot afford the device
+ * synchronisation cudaMalloc/cudaFree may bring.
+ *
+ * lbm_batch_step_static advances n lattices (same precision, each with a
+ * state; their memory is the caller's, e.g. from lbm_create_ext) by `steps`
+ * steps, one batched fused launch per step on cuda_stream, exactly as
+ * lbm_batch_step with tiles of 128 rows.  It allocates no device memory and
+ * calls no allocating library routine: its tile table lives in a file-scope
+ * static device array of LBM_STATIC_BATCH_MAX entries (about 190 KB) that
+ * every GPU loading this library holds until the process exits.
+ *  - n > LBM_STATIC_BATCH_MAX returns LBM_ETOOBIG and does nothing.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, once per device); make that first call before any
+ *    stream capture.
+ *  - Every call shares the one array per device and rewrites the entries it
+ *    uses (nothing in it needs to start at zero); calls whose work overlaps on
+ *    the GPU race on it, so order them (one stream, or events).
+ *  - The caller orders the lattices' own pending work before this call; the
+ *    lattices' current buffers are updated on return (work still in flight
+ *    on cuda_stream). */
+#define LBM_STATIC_BATCH_MAX 256
+int lbm_batch_step_static(int n, lbm_t* const* lattices, int steps, void* cuda_stream);
 
 /* ---- serving: continuous batching of simulation jobs ----------------------
  * Not in the paper.  A job is a Rayleigh-Taylor lattice (size, parameters,

@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 Q = 37
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ESTATE, LBM_ETOOBIG = 0, -1, -2, -3, -4, -5, -6
+LBM_STATIC_BATCH_MAX = 256
 PHASE_PROPAGATE, PHASE_BC, PHASE_COLLIDE, PHASE_ALL = 1, 2, 4, 7
 KERNEL_SEPARATE, KERNEL_FUSED = 0, 1
 PRECISION_FP64, PRECISION_FP32_FP64, PRECISION_FP32_DF = 0, 1, 2
@@ -86,6 +87,7 @@ def load_library():
         "lbm_batch_synchronize": (ctypes.c_int, [vp]),
         "lbm_batch_launch_count": (ctypes.c_int64, [vp]),
         "lbm_batch_destroy": (None, [vp]),
+        "lbm_batch_step_static": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, vp]),
         "lbm_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]),
         "lbm_server_submit": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, ctypes.c_uint64,
                                              ctypes.POINTER(ctypes.c_int64)]),
@@ -114,6 +116,7 @@ def exported_symbols():
             "lbm_launch_count", "lbm_set_timing", "lbm_kernel_times", "lbm_destroy", "lbm_strerror",
             "lbm_batch_create", "lbm_batch_step", "lbm_batch_set_config", "lbm_batch_get_config",
             "lbm_batch_autotune", "lbm_batch_synchronize", "lbm_batch_launch_count", "lbm_batch_destroy",
+            "lbm_batch_step_static",
             "lbm_server_create", "lbm_server_submit", "lbm_server_tick", "lbm_server_poll", "lbm_server_job_state",
             "lbm_server_fetch", "lbm_server_stats_get", "lbm_server_destroy"]
 
@@ -224,6 +227,13 @@ def lbm_kernel_times(h):
 
 def lbm_destroy(h):
     load_library().lbm_destroy(h)
+
+
+def lbm_batch_step_static(handles, steps, cuda_stream):
+    """Advance lattices (lbm_t handles) by `steps` steps without any device
+    allocation; see include/d2q37.h.  cuda_stream is a cudaStream_t value."""
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    _check(load_library().lbm_batch_step_static(len(handles), arr, steps, cuda_stream), "lbm_batch_step_static")
 
 
 # ------------------------------------------------------------------ Lattice

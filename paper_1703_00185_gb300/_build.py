@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libd2q37_gb300.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
-SOURCES = ["d2q37_kernels.cu", "d2q37_kernels_fp32.cu", "d2q37_api.cu", "d2q37_batch.cu", "d2q37_server.cu", "quadrature_dd.cu"]
+SOURCES = ["d2q37_kernels.cu", "d2q37_kernels_fp32.cu", "d2q37_api.cu", "d2q37_batch.cu", "d2q37_batch_static.cu", "d2q37_server.cu", "quadrature_dd.cu"]
 HEADERS = ["d2q37_lattice.cuh", "d2q37_launch.h", "d2q37_handle.h", "dfloat.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -611,6 +611,7 @@ const char* lbm_strerror(int code) {
     case LBM_ECUDA: return "CUDA error";
     case LBM_ETIMEOUT: return "bounded device wait timed out";
     case LBM_ESTATE: return "call out of order (no state yet, or quadrature unavailable)";
+    case LBM_ETOOBIG: return "more lattices than the static table of lbm_batch_step_static holds";
     default: return "unknown error code";
   }
 }
