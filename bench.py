@@ -31,14 +31,16 @@ METRIC = "MLUPS per step"
 UNIT = "MLUPS"
 # algorithmic bytes per site update: 37 populations read + 37 written
 BYTES_PER_SITE = {"fp64": 592, "fp32": 296, "fp32-df": 296}
-# FP64 flops the fused kernel executes per site: DADD + DMUL + 2 DFMA from the
-# ncu instruction counters of the fused kernel (17.15 + 106.06 + 2 x 178.00)
+# FP64 work of the fused kernel per site, from its ncu instruction counters:
+# 17.15 DADD + 106.06 DMUL + 178.00 DFMA = 301.2 FP64 instructions, 479.2 flop
+FP64_INST_PER_SITE = 301.2
 FP64_FLOPS_PER_SITE = 479.2
+# FP64 pipe peak from unit counts and clocks: 2 FP64 instructions per SM per
+# clock (ncu: ...dfma_pred_on.avg.peak_sustained = 2) x 152 SMs x 2.07 GHz
+FP64_PEAK_GINST = 2 * 152 * 2.07
 # DRAM bytes per fused launch at 2048 x 8192, scaled by sites from the ncu
 # capture of the same kernel on 2048 x 1024 (1259.4 MB per launch there)
 FUSED_TRAFFIC_BYTES_2048x8192 = 1259.4e6 * 8
-# FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def parse():
@@ -70,6 +72,25 @@ def parse():
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def replica_seed(rank):
+    """Each rank advances its own lattice (replicas): a different seed per rank."""
+    return 1 + rank
+
+
+def max_over_ranks(torch, dist, ms, device):
+    """The slowest rank's timed region (ms); the value alone without ranks."""
+    if not dist:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(sites_per_rank, world, steps, ms):
+    """Site updates of all ranks over the slowest rank's time, in millions per second."""
+    return sites_per_rank * world * steps / (ms * 1e-3) / 1e6
 
 
 def workload_name(a):
@@ -200,12 +221,16 @@ def roofline_of(kind, avg_s, sites, precision, traffic=None):
            "peak_gbs": hbm_peak, "frac": round(nbytes / avg_s / 1e9 / hbm_peak, 4) if hbm_peak else None,
            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     if precision == "fp64":
-        r = {"bound": "alu", "kernel": kind, "achieved": None, "peak": round(FP64_PEAK_TFLOPS, 4),
-             "unit": "TFLOP/s", "frac": None, "traffic": traffic,
-             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
+        # the FP64 pipe issues DADD, DMUL and DFMA at one rate, so the bound is
+        # counted in FP64 instructions; flops are given beside it
+        r = {"bound": "alu", "kernel": kind, "achieved": None, "peak": round(FP64_PEAK_GINST, 2),
+             "unit": "G FP64 instructions/s", "frac": None, "traffic": traffic,
+             "peak_source": "derived: 2 FP64 instructions/clk/SM x 152 SMs x 2.07 GHz (FP64 pipe)"}
         if kind in ("fused", "collide"):
-            achieved = FP64_FLOPS_PER_SITE * sites / avg_s / 1e12
-            r.update(achieved=round(achieved, 4), frac=round(achieved / FP64_PEAK_TFLOPS, 4))
+            achieved = FP64_INST_PER_SITE * sites / avg_s / 1e9
+            r.update(achieved=round(achieved, 2), frac=round(achieved / FP64_PEAK_GINST, 4),
+                     tflops=round(FP64_FLOPS_PER_SITE * sites / avg_s / 1e12, 4),
+                     fp64_inst_per_site=FP64_INST_PER_SITE, flop_per_site=FP64_FLOPS_PER_SITE)
         r["hbm"] = hbm
     else:
         r = {"bound": "hbm", "kernel": kind, "achieved": hbm["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
@@ -323,14 +348,11 @@ def run_ours(a):
     sites = a.Lx * a.Ly
     uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
     sampler = ClockSampler("GPU-" + str(uuid) if uuid is not None else None)
-    lat, ms, launches, kt, clocks = time_form(torch, lbm, a, dev, a.precision, a.kernel, a.steps, 1 + rank,
-                                              dist, sampler)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    lat, ms, launches, kt, clocks = time_form(torch, lbm, a, dev, a.precision, a.kernel, a.steps,
+                                              replica_seed(rank), dist, sampler)
+    ms = max_over_ranks(torch, dist, ms, dev)
     ms_per_step = ms / a.steps
-    value = sites * world * a.steps / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(sites, world, a.steps, ms)
     kind = max(kt, key=lambda k: kt[k][0])
     traffic = FUSED_TRAFFIC_BYTES_2048x8192 if (kind == "fused" and a.precision == "fp64" and
                                                  (a.Lx, a.Ly) == (2048, 8192)) else None

@@ -413,9 +413,9 @@ __global__ void __launch_bounds__(BY, (D2Q37_FP32_MIN_BLOCKS * 128) / BY) batch_
   int cached = -1;
   for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
     const BatchEntry& e = batch_entry_shared<BY>(tab, n, t, se, cached);
-    const long long local = t - e.tile0;
-    const int x = (int)(local / e.ytiles);
-    const int y = (int)(local - (long long)x * e.ytiles) * BY + threadIdx.x;
+    const int local = (int)(t - e.tile0);  // tiles of one lattice < 2^31: 32-bit division
+    const int x = local / e.ytiles;
+    const int y = (local - x * e.ytiles) * BY + threadIdx.x;
     const int c = e.cur ^ parity;
     if (y < e.p.Ly) fused_site32<W>((const float*)e.buf[c], (float*)e.buf[c ^ 1], e.p, x, y);
   }

@@ -87,15 +87,22 @@ __device__ __forceinline__ dfloat df_rcp(dfloat y) {
 
 __device__ __forceinline__ float df_to_float(dfloat x) { return __fadd_rn(x.hi, x.lo); }
 
+// An integer below 2^23 as a float, exactly, without a conversion instruction
+// (conversions share the slow FP64 pipe on GB300): 2^23 + v has v as its
+// mantissa bits.
+__device__ __forceinline__ float df_small_uint(unsigned v) {
+  return __fsub_rn(__int_as_float(0x4B000000 | v), 8388608.0f);
+}
+
 // Exact-ish conversion of a 64-bit integer scaled by 2^scale_exp: the value
-// is split into 24-bit pieces (each exact in FP32) and summed in df.
+// is split into 23-bit pieces (each exact in FP32) and summed in df.
 __device__ __forceinline__ dfloat df_from_int64(long long v, int scale_exp) {
   const bool neg = v < 0;
   const unsigned long long m = neg ? (unsigned long long)(-v) : (unsigned long long)v;
-  const float a = (float)(unsigned)(m >> 48);               // bits 48..63 (< 2^16)
-  const float b = (float)(unsigned)((m >> 24) & 0xFFFFFF);  // bits 24..47
-  const float c = (float)(unsigned)(m & 0xFFFFFF);          // bits 0..23
-  dfloat r = df_two_sum(__fmul_rn(a, 281474976710656.0f), __fmul_rn(b, 16777216.0f));
+  const float a = df_small_uint((unsigned)(m >> 46));              // bits 46..63 (< 2^18)
+  const float b = df_small_uint((unsigned)((m >> 23) & 0x7FFFFF)); // bits 23..45
+  const float c = df_small_uint((unsigned)(m & 0x7FFFFF));         // bits 0..22
+  dfloat r = df_two_sum(__fmul_rn(a, 70368744177664.0f), __fmul_rn(b, 8388608.0f));  // 2^46, 2^23
   r = df_add(r, c);
   const float s = __int_as_float((scale_exp + 127) << 23);  // 2^scale_exp, scale_exp in [-126, 127]
   r.hi = __fmul_rn(r.hi, s);
