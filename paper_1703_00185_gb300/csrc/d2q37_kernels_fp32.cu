@@ -24,8 +24,11 @@ namespace {
 
 constexpr int kBlockY = 128;
 
+// Resident blocks of 128 threads per SM requested for the FP32 site kernels:
+// 5 caps registers at 96 (16 bytes spilled) and gives 20 warps per SM; on
+// GB300 that ran the fused kernel at 17.1 G sites/s against 15.1 with 4.
 #ifndef D2Q37_FP32_MIN_BLOCKS
-#define D2Q37_FP32_MIN_BLOCKS 4
+#define D2Q37_FP32_MIN_BLOCKS 5
 #endif
 
 __device__ __forceinline__ long long site_index(const StepParams& p, int x, int y) {
@@ -46,6 +49,10 @@ struct WideF64 {
   static __device__ __forceinline__ T mul(T a, float b) { return a * (double)b; }
   static __device__ __forceinline__ T rcp(T a) { return 1.0 / a; }
   static __device__ __forceinline__ float tof(T a) { return (float)a; }
+  // K0 + x2 (K1 + x2 K2) rounded to float
+  static __device__ __forceinline__ float quad(T K0, T K1, T K2, double x2, float, float) {
+    return (float)fma(x2, fma(x2, K2, K1), K0);
+  }
 };
 
 struct WideDF {
@@ -60,6 +67,9 @@ struct WideDF {
   static __device__ __forceinline__ T mul(T a, float b) { return df_mul(a, b); }
   static __device__ __forceinline__ T rcp(T a) { return df_rcp(a); }
   static __device__ __forceinline__ float tof(T a) { return df_to_float(a); }
+  static __device__ __forceinline__ float quad(T K0, T K1, T K2, double, float x2h, float x2l) {
+    return df_to_float(df_quad(K0, K1, K2, {x2h, x2l}));
+  }
 };
 
 // ---- moment sums of the stored deviations in integer arithmetic ------------
@@ -176,21 +186,40 @@ __device__ __forceinline__ Sums deviation_sums(const float (&d)[kQ]) {
 
 // ---- one site ---------------------------------------------------------------
 
+// Float value of an integer sum on the grid 2^ex.
 template <class W>
-struct SiteScalars {
-  typename W::T rho, ux, uy, T, E;  // E = sum |xi|^2 f
-};
+__device__ __forceinline__ float fixed_to_float(long long v, int ex) {
+  return W::tof(W::from_fixed(v, ex));
+}
 
-// rho = 1 + sum d, rho u = s sum c d, 2 rho T = 2 + s^2 sum |c|^2 d - rho |u|^2
-// (sum_l w_l = 1, sum_l w_l c_l = 0, sum_l w_l |xi_l|^2 = D = 2 by the quadrature).
+// BGK collision of one site in deviation form:
+//   d_l' = (1 - omega) d_l + omega w_l (rho P_l - 1),
+//   rho P - 1 = G0_k + rho b (C2_k + b/24) +- rho a (C1_k + b/6), b = a^2,
+// with the shifted fields of Eq. MASTERSHIFT3; G0_k = rho C0_k - 1 is
+// written as K0 + x2_k (K1 + x2_k K2) (C0 is quadratic in x2 = |xi|^2).
+//
+// Which quantities need more than FP32: with d stored to 2^-24 of itself,
+// the result needs errors of that order.  rho and E = sum |xi|^2 f are O(1)
+// sums whose small differences matter (T, the energy change), and G0_k
+// cancels terms of size ~10 near T = 0.5: those take the wide type (K0..K2
+// in their theta-parts, G0_k, rho, E, T).  The velocity (|u| << 1) enters
+// only through a = xi.u_bar and q = |u_bar|^2, whose FP32 errors are scaled
+// down by |u|, and the q-parts of K0, K1 are ~q theta: FP32.
 template <class W>
-__device__ __forceinline__ SiteScalars<W> site_scalars(const float (&d)[kQ]) {
+__device__ __forceinline__ void collide_site32(float (&d)[kQ], const StepParams& p) {
   using T = typename W::T;
   const ShellConsts32& c = c_shell32;
-  SiteScalars<W> o;
-  Sums sm = deviation_sums(d);
-  if (!sm.ok) {  // a deviation of 16 or more (or non-finite): fall back to FP32 sums
-    float s = 0.f, jx = 0.f, jy = 0.f, e = 0.f;
+  const Sums sm = deviation_sums(d);
+  T S, Ec;  // sum d (= rho - 1) and sum |c|^2 d
+  float jx, jy;
+  if (sm.ok) {
+    S = W::from_fixed(sm.s, sm.ex);
+    Ec = W::from_fixed(sm.e, sm.ex);
+    jx = fixed_to_float<W>(sm.jx, sm.ex);
+    jy = fixed_to_float<W>(sm.jy, sm.ex);
+  } else {  // a deviation of 16 or more (or non-finite): FP32 sums
+    float s = 0.f, e = 0.f;
+    jx = jy = 0.f;
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
       s += d[l];
@@ -198,67 +227,42 @@ __device__ __forceinline__ SiteScalars<W> site_scalars(const float (&d)[kQ]) {
       jy += vel_cy(l) * d[l];
       e += (vel_cx(l) * vel_cx(l) + vel_cy(l) * vel_cy(l)) * d[l];
     }
-    o.rho = W::add(W::c(1.0, 1.0f, 0.0f), s);
-    const T inv = W::rcp(o.rho);
-    const T si = W::mul(inv, W::c(c.s, c.s_hi, c.s_lo));
-    o.ux = W::mul(si, W::c(jx, jx, 0.0f));
-    o.uy = W::mul(si, W::c(jy, jy, 0.0f));
-    const T E = W::add(W::c(2.0, 2.0f, 0.0f), W::mul(W::c(c.s2, c.s2_hi, c.s2_lo), e));
-    const T u2 = W::add(W::mul(o.ux, o.ux), W::mul(o.uy, o.uy));
-    o.T = W::mul(W::sub(W::mul(E, inv), u2), 0.5f);
-    o.E = E;
-    return o;
+    S = W::c(s, s, 0.0f);
+    Ec = W::c(e, e, 0.0f);
   }
-  o.rho = W::add(W::c(1.0, 1.0f, 0.0f), W::from_fixed(sm.s, sm.ex));
-  const T inv = W::rcp(o.rho);
-  const T si = W::mul(inv, W::c(c.s, c.s_hi, c.s_lo));
-  o.ux = W::mul(si, W::from_fixed(sm.jx, sm.ex));
-  o.uy = W::mul(si, W::from_fixed(sm.jy, sm.ex));
-  const T E = W::add(W::c(2.0, 2.0f, 0.0f), W::mul(W::c(c.s2, c.s2_hi, c.s2_lo), W::from_fixed(sm.e, sm.ex)));
-  const T u2 = W::add(W::mul(o.ux, o.ux), W::mul(o.uy, o.uy));
-  o.T = W::mul(W::sub(W::mul(E, inv), u2), 0.5f);
-  o.E = E;
-  return o;
-}
-
-// BGK collision of one site in deviation form:
-//   d_l' = (1 - omega) d_l + omega w_l (rho P_l - 1),
-//   rho P - 1 = G0_k + rho b (C2_k + b/24) +- rho a (C1_k + b/6), b = a^2,
-// with the shifted fields of Eq. MASTERSHIFT3 and G0_k = rho C0_k - 1 written
-// as K0 + x2_k (K1 + x2_k K2) (C0 is quadratic in x2 = |xi|^2).
-template <class W>
-__device__ __forceinline__ void collide_site32(float (&d)[kQ], const StepParams& p) {
-  using T = typename W::T;
-  const ShellConsts32& c = c_shell32;
-  const SiteScalars<W> sc = site_scalars<W>(d);
-  const T uby = W::add(sc.uy, W::c(p.uy_shift, p.uy_shift_df[0], p.uy_shift_df[1]));
-  const T q = W::add(W::mul(sc.ux, sc.ux), W::mul(uby, uby));
-  const T th = W::add(sc.T, W::c(p.theta_shift, p.theta_shift_df[0], p.theta_shift_df[1]));
-  const T th2 = W::mul(th, th);
-  // energy change of the collision in c-units, sum |c|^2 (d' - d) =
-  // omega (E_eq - E) / s^2 with E_eq = rho (|u_bar|^2 + D T_bar)
-  const T Eeq = W::mul(sc.rho, W::add(q, W::mul(W::add(th, W::c(1.0, 1.0f, 0.0f)), 2.0f)));
-  const float target_e = p.omega_f * W::tof(W::mul(W::sub(Eeq, sc.E), W::c(c.inv_s2, c.inv_s2_hi, c.inv_s2_lo)));
-  const T thq = W::mul(th, q);
-  // A0 = 1 - q/2 + q^2/8
-  const T A0 = W::add(W::c(1.0, 1.0f, 0.0f), W::mul(q, W::add(W::c(-0.5, -0.5f, 0.0f), W::mul(q, 0.125f))));
-  // rho C0 - 1 = K0 + K1 x2 + K2 x2^2
-  const T K0 = W::add(W::mul(sc.rho, W::add(W::add(W::sub(A0, th), thq), th2)), W::c(-1.0, -1.0f, 0.0f));
-  const T K1 = W::mul(sc.rho, W::sub(W::sub(W::mul(th, 0.5f), W::mul(thq, 0.25f)), th2));
-  const T K2 = W::mul(W::mul(sc.rho, th2), 0.125f);
+  // rho = 1 + sum d, rho u = s sum c d, E = 2 + s^2 sum |c|^2 d, 2 rho T = E - rho |u|^2
+  // (sum_l w_l = 1, sum_l w_l c_l = 0, sum_l w_l |xi_l|^2 = D = 2 by the quadrature)
+  const T rho = W::add(S, 1.0f);
+  const T inv = W::rcp(rho);
+  const float rho_f = W::tof(rho);
+  const float inv_f = W::tof(inv);
+  const float ux = c.s_hi * jx * inv_f;
+  const float uy = c.s_hi * jy * inv_f;
+  const T E = W::add(W::mul(W::c(c.s2, c.s2_hi, c.s2_lo), Ec), 2.0f);
+  const T half_T = W::add(W::mul(E, inv), -(ux * ux + uy * uy));  // 2 T
+  // theta = T_bar - 1 = T - tau^2 g^2 / D - 1
+  const T th = W::add(W::mul(half_T, 0.5f), W::c(p.theta_shift, p.theta_shift_df[0], p.theta_shift_df[1]));
+  const float th_f = W::tof(th);
+  const float uby = uy + p.uy_shift_df[0];
+  const float q = fmaf(ux, ux, uby * uby);
+  const T rth = W::mul(rho, th);
+  const T rth2 = W::mul(rth, th);
+  // rho C0 - 1 = [S - rho theta + rho theta^2 + rho (q (q/8 - 1/2) + theta q)]
+  //            + x2 [rho theta / 2 - rho theta^2 - rho theta q / 4] + x2^2 [rho theta^2 / 8]
+  const float rq = rho_f * q;
+  const T K0 = W::add(W::add(W::sub(S, rth), rth2), rq * (fmaf(0.125f, q, -0.5f) + th_f));
+  const T K1 = W::add(W::sub(W::mul(rth, 0.5f), rth2), -0.25f * rq * th_f);
+  const T K2 = W::mul(rth2, 0.125f);
+  // energy change of the collision in c-units: sum |c|^2 (d' - d) =
+  // omega (E_eq - E) / s^2, E_eq = rho (|u_bar|^2 + D T_bar) = 2 (rho + rho theta) + rho q
+  const float target_e =
+      p.omega_f * c.inv_s2_hi * W::tof(W::add(W::sub(W::mul(W::add(rho, rth), 2.0f), E), rq));
   float G0[kShells];
 #pragma unroll
-  for (int k = 0; k < kShells; ++k) {
-    const T x2 = W::c(c.x2[k], c.x2_hi[k], c.x2_lo[k]);
-    G0[k] = W::tof(W::add(K0, W::mul(x2, W::add(K1, W::mul(x2, K2)))));
-  }
-  const float rho = W::tof(sc.rho);
-  const float thf = W::tof(th);
-  const float qf = W::tof(q);
-  const float sux = W::tof(W::mul(sc.ux, W::c(c.s, c.s_hi, c.s_lo)));
-  const float suy = W::tof(W::mul(uby, W::c(c.s, c.s_hi, c.s_lo)));
-  const float B1 = fmaf(-0.5f, qf, 1.0f);
-  const float B2 = fmaf(-0.25f, qf, 0.5f);
+  for (int k = 0; k < kShells; ++k) G0[k] = W::quad(K0, K1, K2, c.x2[k], c.x2_hi[k], c.x2_lo[k]);
+  const float sux = c.s_hi * ux, suy = c.s_hi * uby;
+  const float B1 = fmaf(-0.5f, q, 1.0f);
+  const float B2 = fmaf(-0.25f, q, 0.5f);
   const float keep = p.keep_f;
   // Collision conserves mass exactly (sum_l w_l P_l = 1).  With FP32 weights
   // and rounding that sum is off by ~1e-8 per site and step, always with the
@@ -271,9 +275,9 @@ __device__ __forceinline__ void collide_site32(float (&d)[kQ], const StepParams&
   for (int k = 1; k < kShells; ++k) {
     float moved_k = 0.0f;
     const float ow = p.omega_f * c.w[k];
-    const float rC1 = rho * fmaf(thf, c.delta[k], B1);
-    const float rC2 = rho * fmaf(thf, c.eps[k], B2);
-    const float r6 = rho * (1.0f / 6.0f), r24 = rho * (1.0f / 24.0f);
+    const float rC1 = rho_f * fmaf(th_f, c.delta[k], B1);
+    const float rC2 = rho_f * fmaf(th_f, c.eps[k], B2);
+    const float r6 = rho_f * (1.0f / 6.0f), r24 = rho_f * (1.0f / 24.0f);
 #pragma unroll
     for (int pr = 0; pr < kPairs; ++pr) {
       if (pair_shell(pr) != k) continue;
@@ -298,6 +302,35 @@ __device__ __forceinline__ void collide_site32(float (&d)[kQ], const StepParams&
 #pragma unroll
   for (int l = 1; l <= 4; ++l) d[l] += fix;
   d[0] -= moved + 4.0f * fix;
+}
+
+// Site fields (FP64) from the stored deviations, for lbm_fields.
+__device__ __forceinline__ void fields_of_site32(const float (&d)[kQ], double& rho, double& ux, double& uy,
+                                                 double& T) {
+  const ShellConsts32& c = c_shell32;
+  const Sums sm = deviation_sums(d);
+  double S, jx, jy, Ec;
+  if (sm.ok) {
+    const double sc = __hiloint2double((sm.ex + 1023) << 20, 0);
+    S = (double)sm.s * sc;
+    jx = (double)sm.jx * sc;
+    jy = (double)sm.jy * sc;
+    Ec = (double)sm.e * sc;
+  } else {
+    S = jx = jy = Ec = 0.0;
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) {
+      S += d[l];
+      jx += vel_cx(l) * (double)d[l];
+      jy += vel_cy(l) * (double)d[l];
+      Ec += (vel_cx(l) * vel_cx(l) + vel_cy(l) * vel_cy(l)) * (double)d[l];
+    }
+  }
+  rho = 1.0 + S;
+  const double inv = 1.0 / rho;
+  ux = c.s * jx * inv;
+  uy = c.s * jy * inv;
+  T = 0.5 * ((2.0 + c.s2 * Ec) * inv - (ux * ux + uy * uy));
 }
 
 // Halo images as in the FP64 store_site.
@@ -475,13 +508,14 @@ __global__ void __launch_bounds__(kBlockY) fields32_kernel(const float* __restri
   float d[kQ];
 #pragma unroll
   for (int l = 0; l < kQ; ++l) d[l] = buf[l * p.plane + i];
-  const SiteScalars<WideF64> sc = site_scalars<WideF64>(d);
+  double r, ux, uy, t;
+  fields_of_site32(d, r, ux, uy, t);
   const long long o = (long long)x * p.Ly + y;
   const long long n = (long long)p.Lx * p.Ly;
-  rho[o] = sc.rho;
-  u[o] = sc.ux;
-  u[n + o] = sc.uy;
-  T[o] = sc.T;
+  rho[o] = r;
+  u[o] = ux;
+  u[n + o] = uy;
+  T[o] = t;
 }
 
 __global__ void __launch_bounds__(kBlockY) plane_to_frame32_kernel(float* __restrict__ frame,

@@ -78,6 +78,12 @@ __device__ __forceinline__ dfloat df_mul(dfloat x, float y) {
 // x * y + z
 __device__ __forceinline__ dfloat df_fma(dfloat x, dfloat y, dfloat z) { return df_add(df_mul(x, y), z); }
 
+// K0 + x (K1 + x K2) (Horner) with sloppy additions.
+__device__ __forceinline__ dfloat df_quad(dfloat K0, dfloat K1, dfloat K2, dfloat x) {
+  const dfloat t = df_add_fast(K1, df_mul(x, K2));
+  return df_add_fast(K0, df_mul(x, t));
+}
+
 // 1 / y: float seed refined by one Newton step in df (error ~ 2^-46 relative).
 __device__ __forceinline__ dfloat df_rcp(dfloat y) {
   const float r = __frcp_rn(y.hi);
