@@ -132,13 +132,27 @@ void fill_step_params(lbm_t* h) {
   const double Tw[2] = {h->prm.T_bot, h->prm.T_top};
   for (int wall = 0; wall < 2; ++wall) {
     equilibrium(g_consts, 1.0, 0.0, 0.0, Tw[wall], sp.fw[wall]);
-    double den = 0.0;
+    for (int l = 0; l < kQ; ++l) {
+      sp.fw32[wall][l] = (float)sp.fw[wall][l];
+      sp.fwmw32[wall][l] = (float)(sp.fw[wall][l] - g_consts.w[kShellOf[l]]);
+    }
+    // D, B, sum_M w and sum_O w over the (row, population) pairs of rows 0..2
+    double den = 0.0, d32 = 0.0, b32 = 0.0, w_miss = 0.0, w_out = 0.0;
     for (int r = 0; r < 3; ++r)
       for (int l = 0; l < kQ; ++l) {
         const bool missing = wall ? (kCy[l] < -r) : (kCy[l] > r);
-        if (missing) den += sp.fw[wall][l];
+        const bool leaving = wall ? (kCy[l] > r) : (kCy[l] < -r);
+        if (missing) {
+          den += sp.fw[wall][l];
+          d32 += sp.fw32[wall][l];
+          b32 += sp.fwmw32[wall][l];
+          w_miss += g_consts.w[kShellOf[l]];
+        }
+        if (leaving) w_out += g_consts.w[kShellOf[l]];
       }
     sp.inv_denom[wall] = 1.0 / den;
+    split_df(b32 - w_out + w_miss, &sp.wall_e32[wall][0], &sp.wall_e32[wall][1]);
+    split_df(1.0 / d32, &sp.wall_inv32[wall][0], &sp.wall_inv32[wall][1]);
   }
 }
 

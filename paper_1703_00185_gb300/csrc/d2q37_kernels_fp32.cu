@@ -352,27 +352,35 @@ __device__ __forceinline__ void store_site32(float* __restrict__ dst, const Step
     }
 }
 
-// Wall bc in deviation form (rows 0..2 from each wall): the outgoing mass
-// sum (w_l + d_l) over the leaving (row, population) pairs of the column, and
-// missing d_l = rho_w f^eq_l(1, 0, T_wall) - w_l; FP64 (wall bands only).
-__device__ __forceinline__ double wall_density32(const float* __restrict__ src, const StepParams& p, int x,
-                                                 int wall) {
-  double out = 0.0;
+// Wall bc in deviation form (rows 0..2 from each wall), in FP32 like the
+// stored values (an FP64 version made the wall warps of small lattices the
+// slowest ones).  The missing deviations are d_l = (rho_w - 1) fw_l + (fw_l - w_l)
+// with FP32 constants fw_l and fw_l - w_l.  rho_w - 1 is solved from the mass
+// balance those rounded constants actually give: with D = sum_M fw_l and
+// B = sum_M (fw_l - w_l) summed exactly, the missing mass sum_M d_l equals the
+// leaving mass sum_O d_l + sum_O w_l - sum_M w_l when
+//   rho_w - 1 = (sum_O d - E) / D,   E = B - sum_O w + sum_M w,
+// with E and 1/D carried as (hi, lo) float pairs, so that no rounding of a
+// constant biases the wall's mass the same way every step.
+__device__ __forceinline__ float wall_rho_minus_1(const float* __restrict__ src, const StepParams& p, int x,
+                                                  int wall) {
+  float out_d = 0.0f;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     const int y = wall ? p.Ly - 1 - r : r;
-    const long long i = site_index(p, x, y);
+    const int i = (int)site_index(p, x, y);
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
       const int cy = vel_cy(l);
-      if (wall ? (cy > r) : (cy < -r)) out += (double)c_shell32.w[vel_shell(l)] + (double)src[l * p.plane + i];
+      if (wall ? (cy > r) : (cy < -r)) out_d += (src + l * p.plane)[i];
     }
   }
-  return out * p.inv_denom[wall];
+  const float t = (out_d - p.wall_e32[wall][0]) - p.wall_e32[wall][1];
+  return fmaf(t, p.wall_inv32[wall][0], t * p.wall_inv32[wall][1]);
 }
 
-__device__ __forceinline__ float missing32(const StepParams& p, double rho_w, int wall, int l) {
-  return (float)(rho_w * p.fw[wall][l] - c_shell32.w64[vel_shell(l)]);
+__device__ __forceinline__ float missing32(const StepParams& p, float rho_w_minus_1, int wall, int l) {
+  return fmaf(rho_w_minus_1, p.fw32[wall][l], p.fwmw32[wall][l]);
 }
 
 __global__ void __launch_bounds__(256) wrap32_kernel(float* __restrict__ buf, StepParams p) {
@@ -417,11 +425,11 @@ __device__ __forceinline__ void fused_site32(const float* __restrict__ src, floa
   if (!p.periodic_y && (y < 3 || y >= p.Ly - 3)) {
     const int wall = y >= p.Ly - 3;
     const int r = wall ? p.Ly - 1 - y : y;
-    const double rho_w = wall_density32(src, p, x, wall);
+    const float rho_w_m1 = wall_rho_minus_1(src, p, x, wall);
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
       const int cy = vel_cy(l);
-      if (wall ? (cy < -r) : (cy > r)) d[l] = missing32(p, rho_w, wall, l);
+      if (wall ? (cy < -r) : (cy > r)) d[l] = missing32(p, rho_w_m1, wall, l);
     }
   }
   collide_site32<W>(d, p);
@@ -470,7 +478,7 @@ __global__ void __launch_bounds__(128) bc32_kernel(const float* __restrict__ src
   if (t >= 2 * p.Lx) return;
   const int wall = t >= p.Lx;
   const int x = t - wall * p.Lx;
-  const double rho_w = wall_density32(src, p, x, wall);
+  const float rho_w_m1 = wall_rho_minus_1(src, p, x, wall);
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     const int y = wall ? p.Ly - 1 - r : r;
@@ -478,7 +486,7 @@ __global__ void __launch_bounds__(128) bc32_kernel(const float* __restrict__ src
 #pragma unroll
     for (int l = 0; l < kQ; ++l) {
       const int cy = vel_cy(l);
-      if (wall ? (cy < -r) : (cy > r)) dst[l * p.plane + i] = missing32(p, rho_w, wall, l);
+      if (wall ? (cy < -r) : (cy > r)) dst[l * p.plane + i] = missing32(p, rho_w_m1, wall, l);
     }
   }
 }

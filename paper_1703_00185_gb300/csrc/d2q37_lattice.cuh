@@ -131,6 +131,11 @@ struct StepParams {
   double theta_shift; // T_bar - 1 - T = -tau^2 g0^2 / D - 1
   double fw[2][kQ];   // wall equilibria f^eq(1, 0, T_wall): [0] bottom, [1] top
   double inv_denom[2];// 1 / sum of fw over the missing (row, population) pairs
+  // the same for the FP32-storage walls, rounded once from FP64:
+  float fw32[2][kQ];    // fw
+  float fwmw32[2][kQ];  // fw - w
+  float wall_e32[2][2];   // (hi, lo): sum_M fwmw32 - sum_O w + sum_M w (M missing, O leaving pairs)
+  float wall_inv32[2][2]; // (hi, lo): 1 / sum_M fw32
 };
 
 // One lattice of a batched launch.  Tiles are one column x by `block_y`
