@@ -39,8 +39,11 @@ FP64_FLOPS_PER_SITE = 479.2
 # clock (ncu: ...dfma_pred_on.avg.peak_sustained = 2) x 152 SMs x 2.07 GHz
 FP64_PEAK_GINST = 2 * 152 * 2.07
 # DRAM bytes per fused launch at 2048 x 8192, scaled by sites from the ncu
-# capture of the same kernel on 2048 x 1024 (1259.4 MB per launch there)
-FUSED_TRAFFIC_BYTES_2048x8192 = 1259.4e6 * 8
+# capture of the same kernel on 2048 x 1024 (1259.7 MB per launch there)
+FUSED_TRAFFIC_BYTES_2048x8192 = 1259.7e6 * 8
+# the same for the FP32-storage double-float kernel, from its capture on
+# 2048 x 2048 (1266.7 MB per launch there)
+FUSED32_DF_TRAFFIC_BYTES_2048x8192 = 1266.7e6 * 4
 
 
 def parse():
@@ -399,7 +402,10 @@ def run_ours(a):
             errs = [float(np.linalg.norm(x - y) / np.linalg.norm(y)) for x, y in zip(fields, ref_fields)]
             forms[prec] = {"value": round(sites * a.steps / (fms * 1e-3) / 1e6, 3), "unit": UNIT,
                            "ms_per_step": round(fms / a.steps, 4), "dtype": DTYPES[prec],
-                           "roofline": roofline_of(fkind, fkt[fkind][0] / fkt[fkind][1] * 1e-3, sites, prec),
+                           "roofline": roofline_of(fkind, fkt[fkind][0] / fkt[fkind][1] * 1e-3, sites, prec,
+                                                   FUSED32_DF_TRAFFIC_BYTES_2048x8192
+                                                   if (fkind == "fused" and prec == "fp32-df" and
+                                                       (a.Lx, a.Ly) == (2048, 8192)) else None),
                            "rel_l2_vs_fp64_after_%d_steps" % a.accuracy_steps:
                                {"rho": errs[0], "u": errs[1], "T": errs[2]},
                            "gpu_launches": fl}
