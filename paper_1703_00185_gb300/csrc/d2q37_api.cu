@@ -28,6 +28,38 @@ void split_df(double v, float* hi, float* lo) {
   *lo = (float)(v - (double)*hi);
 }
 
+// Q55 value of hi + lo (|hi + lo| < 256), each part rounded once.
+long long q55(double hi, double lo) {
+  return std::llround(std::ldexp(hi, 55)) + std::llround(std::ldexp(lo, 55));
+}
+
+// Constants of the fixed-point equilibrium (see StepParams): products and
+// quotients of c_k = omega w_k 2^-E_k in double-double, rounded once to Q55.
+void fill_fixed_consts(StepParams& sp) {
+  const ShellConsts& c = g_consts;
+  for (int k = 0; k < kShells; ++k) {
+    const double wh = sp.omega * c.w[k];
+    const double wl = std::fma(sp.omega, c.w[k], -wh);
+    int E;
+    std::frexp(wh, &E);  // wh = m 2^E, m in [0.5, 1)
+    sp.fx_e[k] = E;
+    const double ch = std::ldexp(wh, -E), cl = std::ldexp(wl, -E);
+    const double mult[6] = {1.0, c.alpha[k], c.beta[k], c.gamma[k], c.delta[k], c.eps[k]};
+    for (int j = 0; j < 6; ++j) {
+      const double ph = ch * mult[j];
+      const double pl = std::fma(ch, mult[j], -ph) + cl * mult[j];
+      sp.fx_c[k][j] = q55(ph, pl);
+    }
+    const double div[2] = {6.0, 24.0};
+    for (int j = 0; j < 2; ++j) {
+      const double qh = ch / div[j];
+      const double ql = (std::fma(-qh, div[j], ch) + cl) / div[j];
+      sp.fx_c[k][6 + j] = q55(qh, ql);
+    }
+  }
+  sp.fx_s = q55(c.s, 0.0);
+}
+
 void solve_once() {
   double s, w[kShells];
   if (!solve_quadrature(&s, w)) return;
@@ -129,6 +161,7 @@ void fill_step_params(lbm_t* h) {
   sp.theta_shift = -(tau * tau * gy * gy) / 2.0 - 1.0;
   split_df(sp.uy_shift, &sp.uy_shift_df[0], &sp.uy_shift_df[1]);
   split_df(sp.theta_shift, &sp.theta_shift_df[0], &sp.theta_shift_df[1]);
+  fill_fixed_consts(sp);
   const double Tw[2] = {h->prm.T_bot, h->prm.T_top};
   for (int wall = 0; wall < 2; ++wall) {
     equilibrium(g_consts, 1.0, 0.0, 0.0, Tw[wall], sp.fw[wall]);

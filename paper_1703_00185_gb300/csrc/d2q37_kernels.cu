@@ -144,6 +144,125 @@ __device__ __forceinline__ double hop_dot(int cx, int cy, const double (&mx)[3],
   return hop_term(cx, mx) + hop_term(cy, my);
 }
 
+// ---- the equilibrium in 64-bit fixed point ---------------------------------
+//
+// GB300 issues 2 FP64 operations per SM per clock; a rounded 64 x 64-bit
+// integer product costs about a quarter of that in issue and runs on the
+// integer pipes.  So the equilibrium of the FP64 step is evaluated in Q55
+// (int64 v stands for v 2^-55, |value| < 256): the per-shell coefficients
+// and the per-pair polynomial in a = xi.u_bar, each product rounded to 2^-55
+// (2.8e-17 absolute on quantities of order 1, below the FP64 rounding of the
+// results).  Per population, the value is turned into an FP64 number with
+// integer operations and relaxed with one FP64 FMA.  The shell factor
+// omega w_k is carried as c_k 2^E_k with c_k in [0.5, 1), so every fixed-point
+// quantity is of order 1.  Sites outside the ranges that keep every
+// intermediate below 256 (rho in (0, 4), |T_bar - 1| < 1, |u_bar| < 0.35 per
+// component) take the FP64 evaluation.
+constexpr int kFx = 55;
+constexpr long long kFxOne = 1LL << kFx;
+
+// a b 2^-55, rounded half up
+__device__ __forceinline__ long long fx_mul(long long a, long long b) {
+  const __int128 prod = (__int128)a * b;
+  return (long long)((prod + ((__int128)1 << (kFx - 1))) >> kFx);
+}
+
+// round(v 2^55) for |v| < 256 (zero and subnormal inputs give 0)
+__device__ __forceinline__ long long to_fx(double v) {
+  const int hi = __double2hiint(v);
+  const unsigned lo = (unsigned)__double2loint(v);
+  const int e = (hi >> 20) & 0x7FF;
+  const long long m = ((long long)((hi & 0xFFFFF) | 0x100000) << 32) | lo;
+  const int sh = e - (1075 - kFx);  // v 2^55 = m 2^sh, sh <= 7 below 256
+  long long r;
+  if (sh >= 0) {
+    r = m << sh;
+  } else {
+    const int rs = min(-sh, 63);
+    r = (m + (1LL << (rs - 1))) >> rs;
+  }
+  r = e ? r : 0;
+  return hi < 0 ? -r : r;
+}
+
+// g 2^(E - 55) as an FP64 number, rounded to nearest (ties away from zero),
+// with integer operations only.
+__device__ __forceinline__ double fx_to_double(long long g, int E) {
+  const unsigned long long sign = (unsigned long long)g & 0x8000000000000000ull;
+  unsigned long long m = g < 0 ? 0ull - (unsigned long long)g : (unsigned long long)g;
+  const int lz = __clzll((long long)m);
+  m <<= (lz & 63);                                             // leading one at bit 63
+  const unsigned long long mant = (m >> 11) + ((m >> 10) & 1);  // 53 bits, leading one at bit 52
+  // value = m 2^(E - 55 - lz) = 1.f 2^(63 + E - 55 - lz); the leading one of
+  // mant adds 1 to the exponent field (and a rounding carry one more)
+  const long long ex = 1023 + 63 - kFx - 1 + E - lz;
+  const unsigned long long bits = ((unsigned long long)ex << 52) + mant;
+  return m ? __longlong_as_double((long long)(bits | sign)) : 0.0;
+}
+
+// c v for a hop component c in -3..3 given the multiples m = {v, 2v, 3v}.
+__device__ __forceinline__ long long fx_hop_term(int c, const long long (&m)[3]) {
+  return c > 0 ? m[c - 1] : -m[-c - 1];
+}
+
+__device__ __forceinline__ long long fx_hop_dot(int cx, int cy, const long long (&mx)[3],
+                                                const long long (&my)[3]) {
+  if (cx == 0) return fx_hop_term(cy, my);
+  if (cy == 0) return fx_hop_term(cx, mx);
+  return fx_hop_term(cx, mx) + fx_hop_term(cy, my);
+}
+
+// The collision of collide_site below with the equilibrium in fixed point.
+// Per shell k (omega w_k = c 2^E, rho-scaled site values rA0 = rho A0, ...):
+//   R0 = c rho C0 = c rA0 + rho theta (c alpha + q c beta + theta c gamma)
+//   R1 = c rho C1 = c rB1 + rho theta c delta,  R2 = c rB2 + rho theta c eps,
+//   R3 = rho c / 6,  R4 = rho c / 24,
+// per pair: even = R0 + b (R2 + b R4), odd = a (R1 + b R3), b = a^2, and
+// f_+- <- (1 - omega) f_+- + (even +- odd) 2^E.  False (f untouched) when the
+// site is outside the fixed-point ranges.
+__device__ __forceinline__ bool collide_site_fx(double (&f)[kQ], const StepParams& p, double rho, double ux,
+                                                double uy, double T) {
+  const double uby = uy + p.uy_shift;
+  const double th = T + p.theta_shift;
+  if (!(rho > 0.0 && rho < 4.0 && fabs(ux) < 0.35 && fabs(uby) < 0.35 && fabs(th) < 1.0)) return false;
+  const long long UX = to_fx(ux), UY = to_fx(uby), R = to_fx(rho), TH = to_fx(th);
+  const long long q = fx_mul(UX, UX) + fx_mul(UY, UY);
+  const long long B1 = kFxOne - (q >> 1);
+  const long long A0 = B1 + (fx_mul(q, q) >> 3);
+  const long long B2 = (kFxOne >> 1) - (q >> 2);
+  const long long rA0 = fx_mul(R, A0), rB1 = fx_mul(R, B1), rB2 = fx_mul(R, B2), rth = fx_mul(R, TH);
+  const long long SX = fx_mul(UX, p.fx_s), SY = fx_mul(UY, p.fx_s);
+  const long long mx[3] = {SX, SX + SX, SX + SX + SX};
+  const long long my[3] = {SY, SY + SY, SY + SY + SY};
+  const double keep = p.one_minus_omega;
+  {
+    const long long* c = p.fx_c[0];
+    const long long R0 = fx_mul(c[0], rA0) + fx_mul(rth, c[1] + fx_mul(q, c[2]) + fx_mul(TH, c[3]));
+    f[0] = fma(keep, f[0], fx_to_double(R0, p.fx_e[0]));
+  }
+#pragma unroll
+  for (int k = 1; k < kShells; ++k) {
+    const long long* c = p.fx_c[k];
+    const int E = p.fx_e[k];
+    const long long R0 = fx_mul(c[0], rA0) + fx_mul(rth, c[1] + fx_mul(q, c[2]) + fx_mul(TH, c[3]));
+    const long long R1 = fx_mul(c[0], rB1) + fx_mul(rth, c[4]);
+    const long long R2 = fx_mul(c[0], rB2) + fx_mul(rth, c[5]);
+    const long long R3 = fx_mul(R, c[6]);
+    const long long R4 = fx_mul(R, c[7]);
+#pragma unroll
+    for (int pr = 0; pr < kPairs; ++pr) {
+      if (pair_shell(pr) != k) continue;
+      const long long a = fx_hop_dot(pair_cx(pr), pair_cy(pr), mx, my);
+      const long long b = fx_mul(a, a);
+      const long long even = R0 + fx_mul(b, R2 + fx_mul(b, R4));
+      const long long odd = fx_mul(a, R1 + fx_mul(b, R3));
+      f[1 + 2 * pr] = fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E));
+      f[2 + 2 * pr] = fma(keep, f[2 + 2 * pr], fx_to_double(even - odd, E));
+    }
+  }
+  return true;
+}
+
 // BGK collision of one site, f <- f - (f - f^eq(rho, u_bar, T_bar)) / tau with
 // u_bar = u + tau g, T_bar = T - tau^2 g^2 / D (Eq. MASTERSHIFT3, Eq. discrete).
 // The equilibrium is evaluated per pair as even +- odd parts with per-shell
@@ -151,6 +270,7 @@ __device__ __forceinline__ double hop_dot(int cx, int cy, const double (&mx)[3],
 __device__ __forceinline__ void collide_site(double (&f)[kQ], const StepParams& p) {
   double rho, ux, uy, T;
   site_moments(f, rho, ux, uy, T);
+  if (collide_site_fx(f, p, rho, ux, uy, T)) return;
   const double ubx = ux;
   const double uby = uy + p.uy_shift;
   const double q = ubx * ubx + uby * uby;
