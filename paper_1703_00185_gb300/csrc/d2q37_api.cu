@@ -28,13 +28,15 @@ void split_df(double v, float* hi, float* lo) {
   *lo = (float)(v - (double)*hi);
 }
 
-// Q55 value of hi + lo (|hi + lo| < 256), each part rounded once.
-long long q55(double hi, double lo) {
-  return std::llround(std::ldexp(hi, 55)) + std::llround(std::ldexp(lo, 55));
+// round((hi + lo) 2^Q) as an unsigned 64-bit integer (0 <= value < 2^64).
+unsigned long long fixed_u64(double hi, double lo, int Q) {
+  const double H = std::ldexp(hi, Q), L = std::ldexp(lo, Q);
+  const double Hr = std::nearbyint(H);
+  return (unsigned long long)Hr + (unsigned long long)std::llround((H - Hr) + L);
 }
 
-// Constants of the fixed-point equilibrium (see StepParams): products and
-// quotients of c_k = omega w_k 2^-E_k in double-double, rounded once to Q55.
+// Constants of the fixed-point equilibrium (see StepParams), from the
+// double-double product omega w_k = (c_k hi + c_k lo) 2^E_k.
 void fill_fixed_consts(StepParams& sp) {
   const ShellConsts& c = g_consts;
   for (int k = 0; k < kShells; ++k) {
@@ -44,20 +46,20 @@ void fill_fixed_consts(StepParams& sp) {
     std::frexp(wh, &E);  // wh = m 2^E, m in [0.5, 1)
     sp.fx_e[k] = E;
     const double ch = std::ldexp(wh, -E), cl = std::ldexp(wl, -E);
-    const double mult[6] = {1.0, c.alpha[k], c.beta[k], c.gamma[k], c.delta[k], c.eps[k]};
-    for (int j = 0; j < 6; ++j) {
-      const double ph = ch * mult[j];
-      const double pl = std::fma(ch, mult[j], -ph) + cl * mult[j];
-      sp.fx_c[k][j] = q55(ph, pl);
-    }
-    const double div[2] = {6.0, 24.0};
-    for (int j = 0; j < 2; ++j) {
-      const double qh = ch / div[j];
-      const double ql = (std::fma(-qh, div[j], ch) + cl) / div[j];
-      sp.fx_c[k][6 + j] = q55(qh, ql);
-    }
+    const double x2 = c.s2 * shell_c2(k);
+    const double x2h = x2, x2l = std::fma(c.s2, (double)shell_c2(k), -x2);  // exact: c.s2 times a small integer
+    // c x2 and c x2^2 in double-double
+    const double p1h = ch * x2h, p1l = std::fma(ch, x2h, -p1h) + (cl * x2h + ch * x2l);
+    const double p2h = p1h * x2h, p2l = std::fma(p1h, x2h, -p2h) + (p1l * x2h + p1h * x2l);
+    sp.fx_ck[k] = fixed_u64(ch, cl, 64);
+    sp.fx_ck2[k] = fixed_u64(p1h, p1l, 60);
+    sp.fx_ck4[k] = fixed_u64(p2h, p2l, 56);
+    const double q6 = ch / 6.0, q6l = (std::fma(-q6, 6.0, ch) + cl) / 6.0;
+    const double q24 = ch / 24.0, q24l = (std::fma(-q24, 24.0, ch) + cl) / 24.0;
+    sp.fx_c6[k] = fixed_u64(q6, q6l, 66);
+    sp.fx_c24[k] = fixed_u64(q24, q24l, 68);
   }
-  sp.fx_s = q55(c.s, 0.0);
+  sp.fx_s62 = fixed_u64(c.s, 0.0, 62);
 }
 
 void solve_once() {

@@ -146,34 +146,60 @@ __device__ __forceinline__ double hop_dot(int cx, int cy, const double (&mx)[3],
 
 // ---- the equilibrium in 64-bit fixed point ---------------------------------
 //
-// GB300 issues 2 FP64 operations per SM per clock; a rounded 64 x 64-bit
-// integer product costs about a quarter of that in issue and runs on the
-// integer pipes.  So the equilibrium of the FP64 step is evaluated in Q55
-// (int64 v stands for v 2^-55, |value| < 256): the per-shell coefficients
-// and the per-pair polynomial in a = xi.u_bar, each product rounded to 2^-55
-// (2.8e-17 absolute on quantities of order 1, below the FP64 rounding of the
-// results).  Per population, the value is turned into an FP64 number with
-// integer operations and relaxed with one FP64 FMA.  The shell factor
-// omega w_k is carried as c_k 2^E_k with c_k in [0.5, 1), so every fixed-point
-// quantity is of order 1.  Sites outside the ranges that keep every
-// intermediate below 256 (rho in (0, 4), |T_bar - 1| < 1, |u_bar| < 0.35 per
-// component) take the FP64 evaluation.
-constexpr int kFx = 55;
-constexpr long long kFxOne = 1LL << kFx;
+// GB300 issues 2 FP64 operations per SM per clock, while the high 64 bits of
+// a 64 x 64-bit integer product take about four IMAD.WIDE on the integer
+// pipes.  So the equilibrium of the FP64 step is evaluated in fixed point:
+// each quantity is an int64 scaled by its own power of two ("Qn": v 2^-n),
+// chosen from its range so that every product is the high word of a 128-bit
+// product (floor rounding) and keeps 2^-55 or better absolute precision on
+// the order-1 quantities; exact integer sums remove the cancellation that
+// limits the FP64 form near T = 0.5 for the outer shells.  Per population
+// the result is turned into an FP64 number with integer operations and
+// relaxed with one FP64 FMA.  The shell factor omega w_k is carried as
+// c_k 2^E_k with c_k in [0.5, 1).  The ranges that keep every intermediate
+// inside its format hold for rho in (0, 4), |T_bar - 1| < 1 and |u_bar| < 0.35
+// per component; other sites take the FP64 evaluation.
+//
+// With K0 = rho (A0 - theta + theta q + theta^2), K1 = rho (theta/2 - theta q/4
+// - theta^2), K2 = rho theta^2 / 8, L0 = rho (B1 - 2 theta), L1 = rho theta / 2,
+// M0 = rho (B2 - 3 theta / 2), M1 = rho theta / 4 (site values), the shell
+// coefficients of collide_site times c_k rho are
+//   R0 = c (K0 + x2 K1 + x2^2 K2),  R1 = c (L0 + x2 L1),  R2 = c (M0 + x2 M1),
+//   R3 = c rho / 6,  R4 = c rho / 24,
+// and per pair even = R0 + b (R2 + b R4), odd = a (R1 + b R3), b = a^2.
+constexpr int kFxOut = 55;  // format of R0 and of the results G = even +- odd
 
-// a b 2^-55, rounded half up
-__device__ __forceinline__ long long fx_mul(long long a, long long b) {
-  const __int128 prod = (__int128)a * b;
-  return (long long)((prod + ((__int128)1 << (kFx - 1))) >> kFx);
+using u64 = unsigned long long;
+
+// floor(x y 2^-64) for signed x, unsigned y
+__device__ __forceinline__ long long mulhi_su(long long x, u64 y) {
+  return (long long)(__umul64hi((u64)x, y) - (x < 0 ? y : 0ull));
 }
 
-// round(v 2^55) for |v| < 256 (zero and subnormal inputs give 0)
+// round(x y 2^-64) (half up) for signed x, unsigned y.  Used where a floor's
+// bias would act the same way every step: the odd part of a pair, whose
+// magnitude a floor after the sign split would always shrink (a momentum
+// damping of 2^-56 per step relative to the odd part).
+__device__ __forceinline__ long long mulhi_su_rn(long long x, u64 y) {
+  const u64 lo = (u64)x * y;
+  return mulhi_su(x, y) + (long long)(lo >> 63);
+}
+
+// floor(x y 2^-sh) for signed x, y and 0 < sh < 64 (the result fits 64 bits)
+__device__ __forceinline__ long long mul_shift(long long x, long long y, int sh) {
+  const u64 h = (u64)__mul64hi(x, y);
+  const u64 l = (u64)x * (u64)y;
+  return (long long)((h << (64 - sh)) | (l >> sh));
+}
+
+// round(v 2^Q) for |v| 2^Q < 2^63 (zero and subnormal inputs give 0)
+template <int Q>
 __device__ __forceinline__ long long to_fx(double v) {
   const int hi = __double2hiint(v);
   const unsigned lo = (unsigned)__double2loint(v);
   const int e = (hi >> 20) & 0x7FF;
   const long long m = ((long long)((hi & 0xFFFFF) | 0x100000) << 32) | lo;
-  const int sh = e - (1075 - kFx);  // v 2^55 = m 2^sh, sh <= 7 below 256
+  const int sh = e - (1075 - Q);  // v 2^Q = m 2^sh, sh <= 10 below 2^63
   long long r;
   if (sh >= 0) {
     r = m << sh;
@@ -188,15 +214,15 @@ __device__ __forceinline__ long long to_fx(double v) {
 // g 2^(E - 55) as an FP64 number, rounded to nearest (ties away from zero),
 // with integer operations only.
 __device__ __forceinline__ double fx_to_double(long long g, int E) {
-  const unsigned long long sign = (unsigned long long)g & 0x8000000000000000ull;
-  unsigned long long m = g < 0 ? 0ull - (unsigned long long)g : (unsigned long long)g;
+  const u64 sign = (u64)g & 0x8000000000000000ull;
+  u64 m = g < 0 ? 0ull - (u64)g : (u64)g;
   const int lz = __clzll((long long)m);
-  m <<= (lz & 63);                                             // leading one at bit 63
-  const unsigned long long mant = (m >> 11) + ((m >> 10) & 1);  // 53 bits, leading one at bit 52
-  // value = m 2^(E - 55 - lz) = 1.f 2^(63 + E - 55 - lz); the leading one of
-  // mant adds 1 to the exponent field (and a rounding carry one more)
-  const long long ex = 1023 + 63 - kFx - 1 + E - lz;
-  const unsigned long long bits = ((unsigned long long)ex << 52) + mant;
+  m <<= (lz & 63);                              // leading one at bit 63
+  const u64 mant = (m >> 11) + ((m >> 10) & 1);  // 53 bits, leading one at bit 52
+  // value = 1.f 2^(63 + E - 55 - lz); the leading one of mant adds 1 to the
+  // exponent field (and a rounding carry one more)
+  const long long ex = 1023 + 63 - kFxOut - 1 + E - lz;
+  const u64 bits = ((u64)ex << 52) + mant;
   return m ? __longlong_as_double((long long)(bits | sign)) : 0.0;
 }
 
@@ -212,50 +238,62 @@ __device__ __forceinline__ long long fx_hop_dot(int cx, int cy, const long long 
   return fx_hop_term(cx, mx) + fx_hop_term(cy, my);
 }
 
-// The collision of collide_site below with the equilibrium in fixed point.
-// Per shell k (omega w_k = c 2^E, rho-scaled site values rA0 = rho A0, ...):
-//   R0 = c rho C0 = c rA0 + rho theta (c alpha + q c beta + theta c gamma)
-//   R1 = c rho C1 = c rB1 + rho theta c delta,  R2 = c rB2 + rho theta c eps,
-//   R3 = rho c / 6,  R4 = rho c / 24,
-// per pair: even = R0 + b (R2 + b R4), odd = a (R1 + b R3), b = a^2, and
-// f_+- <- (1 - omega) f_+- + (even +- odd) 2^E.  False (f untouched) when the
-// site is outside the fixed-point ranges.
+// The collision of collide_site below with the equilibrium in fixed point
+// (formats in the comments).  False (f untouched) when the site is outside
+// the fixed-point ranges.
 __device__ __forceinline__ bool collide_site_fx(double (&f)[kQ], const StepParams& p, double rho, double ux,
                                                 double uy, double T) {
   const double uby = uy + p.uy_shift;
   const double th = T + p.theta_shift;
   if (!(rho > 0.0 && rho < 4.0 && fabs(ux) < 0.35 && fabs(uby) < 0.35 && fabs(th) < 1.0)) return false;
-  const long long UX = to_fx(ux), UY = to_fx(uby), R = to_fx(rho), TH = to_fx(th);
-  const long long q = fx_mul(UX, UX) + fx_mul(UY, UY);
-  const long long B1 = kFxOne - (q >> 1);
-  const long long A0 = B1 + (fx_mul(q, q) >> 3);
-  const long long B2 = (kFxOne >> 1) - (q >> 2);
-  const long long rA0 = fx_mul(R, A0), rB1 = fx_mul(R, B1), rB2 = fx_mul(R, B2), rth = fx_mul(R, TH);
-  const long long SX = fx_mul(UX, p.fx_s), SY = fx_mul(UY, p.fx_s);
-  const long long mx[3] = {SX, SX + SX, SX + SX + SX};
+  const long long UX = to_fx<64>(ux), UY = to_fx<64>(uby);  // Q64
+  const long long TH = to_fx<62>(th);                        // Q62
+  const u64 R = (u64)to_fx<61>(rho);                         // Q61
+  const u64 AUX = UX < 0 ? 0ull - (u64)UX : (u64)UX, AUY = UY < 0 ? 0ull - (u64)UY : (u64)UY;
+  const u64 q = __umul64hi(AUX, AUX) + __umul64hi(AUY, AUY);  // Q64
+  const u64 q2 = __umul64hi(q, q);                            // Q64
+  const u64 B1 = (1ull << 62) - (q >> 3);                     // Q62: 1 - q/2
+  const u64 B2 = (1ull << 61) - (q >> 4);                     //      1/2 - q/4
+  const u64 A0 = B1 + (q2 >> 5);                              //      1 - q/2 + q^2/8
+  const long long SX = mulhi_su(UX, p.fx_s62), SY = mulhi_su(UY, p.fx_s62);  // Q62
+  const long long rA0 = (long long)__umul64hi(R, A0);        // Q59
+  const long long rB1 = (long long)__umul64hi(R, B1);        // Q59
+  const long long rB2 = (long long)__umul64hi(R, B2);        // Q59
+  const long long rth = mul_shift((long long)R, TH, 62);     // Q61: rho theta
+  const long long rth2 = mul_shift(rth, TH, 62);             // Q61: rho theta^2
+  const long long rthq = mulhi_su(rth, q);                   // Q61: rho theta q
+  const long long K0 = rA0 - (rth >> 2) + (rthq >> 2) + (rth2 >> 2);  // Q59
+  const long long K1 = (rth >> 2) - (rthq >> 3) - (rth2 >> 1);        // Q60
+  const u64 K2 = (u64)rth2;                                           // Q64 (rho theta^2 / 8)
+  const long long L0 = rB1 - (rth >> 1);                              // Q59
+  const long long L1 = rth;                                           // Q62 (rho theta / 2)
+  const long long M0 = rB2 - (rth >> 2) - (rth >> 3);                 // Q59
+  const long long M1 = rth;                                           // Q63 (rho theta / 4)
+  const long long mx[3] = {SX, SX + SX, SX + SX + SX};                // Q62
   const long long my[3] = {SY, SY + SY, SY + SY + SY};
   const double keep = p.one_minus_omega;
-  {
-    const long long* c = p.fx_c[0];
-    const long long R0 = fx_mul(c[0], rA0) + fx_mul(rth, c[1] + fx_mul(q, c[2]) + fx_mul(TH, c[3]));
-    f[0] = fma(keep, f[0], fx_to_double(R0, p.fx_e[0]));
-  }
+  f[0] = fma(keep, f[0], fx_to_double(mulhi_su(K0, p.fx_ck[0]) >> 4, p.fx_e[0]));  // x2 = 0
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
-    const long long* c = p.fx_c[k];
+    const u64 ck = p.fx_ck[k], ck2 = p.fx_ck2[k];
+    const long long R0 = (mulhi_su(K0, ck) >> 4) + (mulhi_su(K1, ck2) >> 1) +
+                         ((long long)__umul64hi(K2, p.fx_ck4[k]) >> 1);                // Q55
+    const long long R1 = (mulhi_su(L0, ck) >> 2) + (mulhi_su(L1, ck2) >> 1);          // Q57
+    const long long R2 = mulhi_su(M0, ck) + mulhi_su(M1, ck2);                        // Q59
+    const u64 R3 = __umul64hi(R, p.fx_c6[k]);                                         // Q63
+    const u64 R4 = __umul64hi(R, p.fx_c24[k]);                                        // Q65
     const int E = p.fx_e[k];
-    const long long R0 = fx_mul(c[0], rA0) + fx_mul(rth, c[1] + fx_mul(q, c[2]) + fx_mul(TH, c[3]));
-    const long long R1 = fx_mul(c[0], rB1) + fx_mul(rth, c[4]);
-    const long long R2 = fx_mul(c[0], rB2) + fx_mul(rth, c[5]);
-    const long long R3 = fx_mul(R, c[6]);
-    const long long R4 = fx_mul(R, c[7]);
 #pragma unroll
     for (int pr = 0; pr < kPairs; ++pr) {
       if (pair_shell(pr) != k) continue;
-      const long long a = fx_hop_dot(pair_cx(pr), pair_cy(pr), mx, my);
-      const long long b = fx_mul(a, a);
-      const long long even = R0 + fx_mul(b, R2 + fx_mul(b, R4));
-      const long long odd = fx_mul(a, R1 + fx_mul(b, R3));
+      const long long a = fx_hop_dot(pair_cx(pr), pair_cy(pr), mx, my);  // Q62
+      const u64 A = a < 0 ? 0ull - (u64)a : (u64)a;
+      const u64 b = __umul64hi(A, A);                                    // Q60
+      const long long t = R2 + (long long)(__umul64hi(b, R4) >> 2);     // Q59
+      const long long even = R0 + mulhi_su(t, b);                        // Q55
+      const long long s = R1 + (long long)(__umul64hi(b, R3) >> 2);     // Q57
+      const long long oa = mulhi_su_rn(s, A);                            // Q55: |a| (R1 + b R3)
+      const long long odd = a < 0 ? -oa : oa;
       f[1 + 2 * pr] = fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E));
       f[2 + 2 * pr] = fma(keep, f[2 + 2 * pr], fx_to_double(even - odd, E));
     }

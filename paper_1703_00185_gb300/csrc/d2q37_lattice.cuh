@@ -136,12 +136,12 @@ struct StepParams {
   float fwmw32[2][kQ];  // fw - w
   float wall_e32[2][2];   // (hi, lo): sum_M fwmw32 - sum_O w + sum_M w (M missing, O leaving pairs)
   float wall_inv32[2][2]; // (hi, lo): 1 / sum_M fw32
-  // Fixed-point (Q55) equilibrium constants of the FP64 step: per shell k,
-  // omega w_k = c_k 2^fx_e[k] with c_k in [0.5, 1), and
-  // fx_c[k] = {c, c alpha, c beta, c gamma, c delta, c eps, c/6, c/24}_k.
-  long long fx_c[kShells][8];
+  // Fixed-point equilibrium constants of the FP64 step: per shell k,
+  // omega w_k = c_k 2^fx_e[k] with c_k in [0.5, 1); as unsigned integers
+  // c 2^64, c x2 2^60, c x2^2 2^56, (c/6) 2^66, (c/24) 2^68 (x2 = s^2 |c_l|^2).
+  unsigned long long fx_ck[kShells], fx_ck2[kShells], fx_ck4[kShells], fx_c6[kShells], fx_c24[kShells];
   int fx_e[kShells];
-  long long fx_s;   // the velocity scale s
+  unsigned long long fx_s62;  // s 2^62
 };
 
 // One lattice of a batched launch.  Tiles are one column x by `block_y`
