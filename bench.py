@@ -33,14 +33,15 @@ UNIT = "MLUPS"
 BYTES_PER_SITE = {"fp64": 592, "fp32": 296, "fp32-df": 296}
 # FP64 work of the fused kernel per site, from its ncu instruction counters:
 # 17.15 DADD + 106.06 DMUL + 178.00 DFMA = 301.2 FP64 instructions, 479.2 flop
-FP64_INST_PER_SITE = 301.2
-FP64_FLOPS_PER_SITE = 479.2
+# FP64-pipe instructions per site of the fused FP64 kernel (ncu on 2048 x 1024:
+# DFMA + DMUL + DADD + DSETP + the integer-to-FP64 conversions)
+FP64_PIPE_INST_PER_SITE = 104.6
 # FP64 pipe peak from unit counts and clocks: 2 FP64 instructions per SM per
 # clock (ncu: ...dfma_pred_on.avg.peak_sustained = 2) x 152 SMs x 2.07 GHz
 FP64_PEAK_GINST = 2 * 152 * 2.07
 # DRAM bytes per fused launch at 2048 x 8192, scaled by sites from the ncu
-# capture of the same kernel on 2048 x 1024 (1259.7 MB per launch there)
-FUSED_TRAFFIC_BYTES_2048x8192 = 1259.7e6 * 8
+# capture of the same kernel on 2048 x 1024 (1257.5 MB per launch there)
+FUSED_TRAFFIC_BYTES_2048x8192 = 1257.5e6 * 8
 # the same for the FP32-storage double-float kernel, from its capture on
 # 2048 x 2048 (1266.7 MB per launch there)
 FUSED32_DF_TRAFFIC_BYTES_2048x8192 = 1266.7e6 * 4
@@ -215,29 +216,24 @@ DTYPES = {"fp64": "f64", "fp32": "f32 storage + f64 wide terms", "fp32-df": "f32
 
 
 def roofline_of(kind, avg_s, sites, precision, traffic=None):
-    """Roofline entry of the dominant kernel: FP64-pipe bound for the FP64 form,
-    HBM bound for the FP32-storage forms."""
+    """Roofline entry of the dominant kernel: the HBM bound (algorithmic bytes
+    per site over the measured copy bandwidth).  For the FP64 form the FP64
+    pipe's share is given beside it (FP64-pipe instructions per site counted
+    by ncu on the same kernel)."""
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     nbytes = (BYTES_PER_SITE[precision] if kind in ("fused", "propagate", "collide") else 0) * sites
-    hbm = {"algorithmic_bytes_per_launch": nbytes, "achieved_gbs": round(nbytes / avg_s / 1e9, 1),
-           "peak_gbs": hbm_peak, "frac": round(nbytes / avg_s / 1e9 / hbm_peak, 4) if hbm_peak else None,
-           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    if precision == "fp64":
-        # the FP64 pipe issues DADD, DMUL and DFMA at one rate, so the bound is
-        # counted in FP64 instructions; flops are given beside it
-        r = {"bound": "alu", "kernel": kind, "achieved": None, "peak": round(FP64_PEAK_GINST, 2),
-             "unit": "G FP64 instructions/s", "frac": None, "traffic": traffic,
-             "peak_source": "derived: 2 FP64 instructions/clk/SM x 152 SMs x 2.07 GHz (FP64 pipe)"}
-        if kind in ("fused", "collide"):
-            achieved = FP64_INST_PER_SITE * sites / avg_s / 1e9
-            r.update(achieved=round(achieved, 2), frac=round(achieved / FP64_PEAK_GINST, 4),
-                     tflops=round(FP64_FLOPS_PER_SITE * sites / avg_s / 1e12, 4),
-                     fp64_inst_per_site=FP64_INST_PER_SITE, flop_per_site=FP64_FLOPS_PER_SITE)
-        r["hbm"] = hbm
-    else:
-        r = {"bound": "hbm", "kernel": kind, "achieved": hbm["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
-             "frac": hbm["frac"], "traffic": traffic, "peak_source": hbm["peak_source"]}
+    achieved = nbytes / avg_s / 1e9
+    r = {"bound": "hbm", "kernel": kind, "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+         "frac": round(achieved / hbm_peak, 4) if hbm_peak else None, "traffic": traffic,
+         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+         "algorithmic_bytes_per_launch": nbytes}
+    if precision == "fp64" and kind in ("fused", "collide"):
+        ginst = FP64_PIPE_INST_PER_SITE * sites / avg_s / 1e9
+        r["fp64_pipe"] = {"inst_per_site": FP64_PIPE_INST_PER_SITE, "achieved": round(ginst, 2),
+                          "peak": round(FP64_PEAK_GINST, 2), "unit": "G FP64-pipe instructions/s",
+                          "frac": round(ginst / FP64_PEAK_GINST, 4),
+                          "peak_source": "derived: 2 FP64-pipe instructions/clk/SM x 152 SMs x 2.07 GHz"}
     r["avg_launch_ms"] = round(avg_s * 1e3, 4)
     return r
 
