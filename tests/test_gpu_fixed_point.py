@@ -1,0 +1,118 @@
+"""The FP64 step evaluates the equilibrium in 64-bit fixed point where every
+intermediate fits its format (rho in (0, 4), |T_bar - 1| < 1, |u_bar| < 0.35
+per component) and in FP64 elsewhere.  These tests put sites on both sides
+of those limits, inside the same warps, and hold both paths to the oracle;
+and they check that the fixed-point rounding carries no bias a long run
+would accumulate (a uniform flow must keep its momentum and mass)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1703_00185_gb300 as lbm
+from tests import synthetic
+
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-14
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_00185_gb300 import _build
+    _build.build()
+    lbm.load_library()
+
+
+@pytest.fixture(scope="module")
+def perm():
+    cx, cy = lbm.lbm_velocity_set()
+    ocx, ocy = oracle.velocity_set()
+    idx = {(a, b): i for i, (a, b) in enumerate(zip(ocx.tolist(), ocy.tolist()))}
+    return np.array([idx[(a, b)] for a, b in zip(cx.tolist(), cy.tolist())])
+
+
+def plane_rel_err(a, b):
+    a, b = a.reshape(37, -1), b.reshape(37, -1)
+    return float(np.max(np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)))
+
+
+def outside(rho, ux, uy, T, tau, g0):
+    """Sites the fixed-point form does not take (host copy of its test)."""
+    uby = uy - tau * g0
+    th = T - (tau * g0) ** 2 / 2 - 1.0
+    return ~((rho > 0) & (rho < 4) & (np.abs(ux) < 0.35) & (np.abs(uby) < 0.35) & (np.abs(th) < 1))
+
+
+def collide_once(perm, rho, ux, uy, T, tau, g0):
+    Lx, Ly = rho.shape
+    o = oracle.Lattice(Lx, Ly, tau=tau, g0=g0)
+    g = lbm.Lattice(Lx, Ly, tau=tau, g0=g0, kernel="separate", device="cuda:0")
+    o.set_equilibrium(rho, ux, uy, T)
+    f = o.populations() * (1.0 + 0.01 * (2.0 * np.random.default_rng(7).random((37, Lx, Ly)) - 1.0))
+    o.set_populations(f)
+    g.set_populations(f[perm])
+    o.run(1, oracle.PHASE_COLLIDE)
+    g.run_phases(1, lbm.PHASE_COLLIDE)
+    return g.populations(), o.populations()[perm]
+
+
+@pytest.mark.parametrize("tau,g0", [(0.8, 1e-4), (0.6, 1e-3), (1.4, 0.0)])
+def test_collide_across_the_fixed_point_ranges(tau, g0, perm):
+    Lx, Ly = 40, 96
+    rho, ux, uy, T = synthetic.random_fields(Lx, Ly, 21, rho=(0.3, 5.0), u=0.5, T=(0.3, 2.4))
+    frac = float(outside(rho, ux, uy, T, tau, g0).mean())
+    assert 0.2 < frac < 0.8, frac  # both paths, mixed inside warps
+    a, b = collide_once(perm, rho, ux, uy, T, tau, g0)
+    assert plane_rel_err(a, b) <= POP_TOL
+
+
+def test_collide_at_the_range_limits(perm):
+    """Sites just inside and just outside each limit (the moments the kernel
+    computes differ from the set fields by rounding only)."""
+    Lx, Ly = 8, 32
+    rho = np.full((Lx, Ly), 1.0)
+    ux = np.full((Lx, Ly), 0.01)
+    uy = np.full((Lx, Ly), -0.02)
+    T = np.full((Lx, Ly), 1.0)
+    eps = 1e-6
+    for j, (r, u, v, t) in enumerate([(4 - eps, 0.0, 0.0, 1.0), (4 + eps, 0.0, 0.0, 1.0),
+                                      (1.0, 0.35 - eps, 0.0, 1.0), (1.0, 0.35 + eps, 0.0, 1.0),
+                                      (1.0, -0.35 + eps, 0.0, 1.0), (1.0, -0.35 - eps, 0.0, 1.0),
+                                      (1.0, 0.0, 0.35 - eps, 1.0), (1.0, 0.0, -0.35 - eps, 1.0),
+                                      (1.0, 0.0, 0.0, 2.0 - eps), (1.0, 0.0, 0.0, 2.0 + eps),
+                                      (1.0, 0.0, 0.0, 1e-3 + eps), (0.05, 0.3, -0.3, 1.9)]):
+        rho[:, j] = r
+        ux[:, j] = u
+        uy[:, j] = v
+        T[:, j] = t
+    a, b = collide_once(perm, rho, ux, uy, T, 0.8, 0.0)
+    assert plane_rel_err(a, b) <= POP_TOL
+
+
+@pytest.mark.parametrize("kernel", ["fused", "separate"])
+def test_uniform_flow_keeps_momentum_and_mass(kernel):
+    """A uniform equilibrium without gravity is a fixed point of the step:
+    after 2000 steps its velocity, density and temperature must still be the
+    initial ones.  A rounding bias in the fixed-point odd part would damp
+    the momentum by ~1e-15 per step (a floor after the sign split did: 1.8e-12
+    after 2000 steps); unbiased rounding leaves noise of ~1e-13."""
+    Lx, Ly = 32, 64
+    u0 = (0.1, -0.06)
+    g = lbm.Lattice(Lx, Ly, tau=0.8, g0=0.0, periodic_y=True, kernel=kernel, device="cuda:0")
+    o = oracle.Lattice(Lx, Ly, tau=0.8, g0=0.0, periodic_y=True)
+    o.set_equilibrium(np.full((Lx, Ly), 1.1), np.full((Lx, Ly), u0[0]), np.full((Lx, Ly), u0[1]),
+                      np.full((Lx, Ly), 0.9))
+    cx, cy = lbm.lbm_velocity_set()
+    ocx, ocy = oracle.velocity_set()
+    idx = {(a, b): i for i, (a, b) in enumerate(zip(ocx.tolist(), ocy.tolist()))}
+    g.set_populations(o.populations()[np.array([idx[(a, b)] for a, b in zip(cx.tolist(), cy.tolist())])])
+    rho0, _, _ = g.fields()
+    g.step(2000)
+    rho, u, T = g.fields()
+    assert np.max(np.abs(u[0] - u0[0])) / abs(u0[0]) < 5e-13
+    assert np.max(np.abs(u[1] - u0[1])) / abs(u0[1]) < 5e-13
+    assert abs(rho.sum() - rho0.sum()) / rho0.sum() < 1e-13
+    assert np.max(np.abs(T - 0.9)) < 1e-12
