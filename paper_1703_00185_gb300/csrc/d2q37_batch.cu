@@ -21,6 +21,7 @@ struct lbm_batch_t {
   std::vector<lbm_t*> lat;
   std::vector<BatchEntry> host_tab[3];  // per block_y choice (64, 128, 256)
   BatchEntry* dev_tab[3];
+  int* dev_tile_entry[3];  // owning entry of every tile
   long long tiles[3];
   int block_y;        // 64, 128 or 256
   int blocks_per_sm;  // 0: one block per tile; else a persistent grid of blocks_per_sm x SMs
@@ -55,8 +56,9 @@ int launch(lbm_batch_t* b, int block_y, int blocks_per_sm, int parity) {
   const int s = slot_of(block_y);
   const int grid = (int)grid_of(b, block_y, blocks_per_sm);
   const int n = b->prec == LBM_PRECISION_FP64
-                    ? launch_batch_fused(b->dev_tab[s], b->n, b->tiles[s], parity, block_y, grid, b->stream)
-                    : launch_batch_fused32(b->dev_tab[s], b->n, b->tiles[s], parity, block_y, grid,
+                    ? launch_batch_fused(b->dev_tab[s], b->dev_tile_entry[s], b->n, b->tiles[s], parity, block_y,
+                                         grid, b->stream)
+                    : launch_batch_fused32(b->dev_tab[s], b->dev_tile_entry[s], b->n, b->tiles[s], parity, block_y, grid,
                                            b->prec == LBM_PRECISION_FP32_FP64, b->stream);
   if (n < 0) return LBM_ECUDA;
   b->launches += n;
@@ -149,13 +151,27 @@ int lbm_batch_create(int n, lbm_t* const* lattices, void* cuda_stream, lbm_batch
       t0 += (long long)lattices[i]->Lx * e.ytiles;
     }
     b->tiles[s] = t0;
-    if (cudaMalloc(&b->dev_tab[s], n * sizeof(BatchEntry)) != cudaSuccess) {
+    if (t0 > 2147483647LL) {
+      rc = LBM_ETOOBIG;
+      break;
+    }
+    std::vector<int> owner((size_t)t0);
+    for (int i = 0; i < n; ++i)
+      std::fill(owner.begin() + b->host_tab[s][i].tile0,
+                owner.begin() + b->host_tab[s][i].tile0 + (long long)lattices[i]->Lx * b->host_tab[s][i].ytiles, i);
+    if (cudaMalloc(&b->dev_tab[s], n * sizeof(BatchEntry)) != cudaSuccess ||
+        cudaMalloc(&b->dev_tile_entry[s], owner.size() * sizeof(int)) != cudaSuccess) {
       cudaGetLastError();
       rc = LBM_ENOMEM;
       break;
     }
     rc = check(cudaMemcpyAsync(b->dev_tab[s], b->host_tab[s].data(), n * sizeof(BatchEntry),
                                cudaMemcpyHostToDevice, b->stream));
+    if (!rc)
+      rc = check(cudaMemcpyAsync(b->dev_tile_entry[s], owner.data(), owner.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, b->stream));
+    // the host vector must outlive the asynchronous copy
+    if (!rc) rc = check(cudaStreamSynchronize(b->stream));
   }
   if (!rc) rc = check(cudaStreamSynchronize(b->stream));
   if (rc) {
@@ -263,6 +279,8 @@ void lbm_batch_destroy(lbm_batch_t* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->graph2) cudaGraphExecDestroy(b->graph2);
   for (BatchEntry* t : b->dev_tab)
+    if (t) cudaFree(t);
+  for (int* t : b->dev_tile_entry)
     if (t) cudaFree(t);
   delete b;
 }

@@ -449,11 +449,9 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_FP32_MIN_BLOCKS) fused32_kernel
 // Many lattices in one launch (see batch_fused_kernel of the FP64 kernels).
 template <class W, int BY>
 __global__ void __launch_bounds__(BY, (D2Q37_FP32_MIN_BLOCKS * 128) / BY) batch_fused32_kernel(
-    const BatchEntry* __restrict__ tab, int n, long long tiles, int parity) {
-  __shared__ BatchEntry se;
-  int cached = -1;
+    const BatchEntry* __restrict__ tab, const int* __restrict__ tile_entry, int n, long long tiles, int parity) {
   for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const BatchEntry& e = batch_entry_shared<BY>(tab, n, t, se, cached);
+    const BatchEntry& e = tab[tile_entry ? tile_entry[t] : batch_entry_of(tab, n, t)];
     const int local = (int)(t - e.tile0);  // tiles of one lattice < 2^31: 32-bit division
     const int x = local / e.ytiles;
     const int y = (local - x * e.ytiles) * BY + threadIdx.x;
@@ -599,8 +597,9 @@ int launch_fused32(const float* src, float* dst, const StepParams& p, bool wide_
 }
 
 template <class W, int BY>
-int batch32_launch(const BatchEntry* tab, int n, long long tiles, int parity, int grid, cudaStream_t stream) {
-  batch_fused32_kernel<W, BY><<<grid, BY, 0, stream>>>(tab, n, tiles, parity);
+int batch32_launch(const BatchEntry* tab, const int* tile_entry, int n, long long tiles, int parity, int grid,
+                   cudaStream_t stream) {
+  batch_fused32_kernel<W, BY><<<grid, BY, 0, stream>>>(tab, tile_entry, n, tiles, parity);
   return done(1);
 }
 
@@ -611,15 +610,15 @@ int batch32_occupancy() {
   return b;
 }
 
-int launch_batch_fused32(const BatchEntry* tab, int n, long long tiles, int parity, int block_y, int grid,
-                         bool wide_fp64, cudaStream_t stream) {
+int launch_batch_fused32(const BatchEntry* tab, const int* tile_entry, int n, long long tiles, int parity,
+                         int block_y, int grid, bool wide_fp64, cudaStream_t stream) {
   switch (block_y) {
-    case 64: return wide_fp64 ? batch32_launch<WideF64, 64>(tab, n, tiles, parity, grid, stream)
-                              : batch32_launch<WideDF, 64>(tab, n, tiles, parity, grid, stream);
-    case 128: return wide_fp64 ? batch32_launch<WideF64, 128>(tab, n, tiles, parity, grid, stream)
-                               : batch32_launch<WideDF, 128>(tab, n, tiles, parity, grid, stream);
-    case 256: return wide_fp64 ? batch32_launch<WideF64, 256>(tab, n, tiles, parity, grid, stream)
-                               : batch32_launch<WideDF, 256>(tab, n, tiles, parity, grid, stream);
+    case 64: return wide_fp64 ? batch32_launch<WideF64, 64>(tab, tile_entry, n, tiles, parity, grid, stream)
+                              : batch32_launch<WideDF, 64>(tab, tile_entry, n, tiles, parity, grid, stream);
+    case 128: return wide_fp64 ? batch32_launch<WideF64, 128>(tab, tile_entry, n, tiles, parity, grid, stream)
+                               : batch32_launch<WideDF, 128>(tab, tile_entry, n, tiles, parity, grid, stream);
+    case 256: return wide_fp64 ? batch32_launch<WideF64, 256>(tab, tile_entry, n, tiles, parity, grid, stream)
+                               : batch32_launch<WideDF, 256>(tab, tile_entry, n, tiles, parity, grid, stream);
     default: return -1;
   }
 }

@@ -167,24 +167,6 @@ __device__ __forceinline__ int batch_entry_of(const BatchEntry* __restrict__ tab
   return lo;
 }
 
-// The entry owning tile t, staged in shared memory `se` by the whole block
-// (all threads call this with the same t); `cached` remembers which entry is
-// staged, so consecutive tiles of one lattice copy it once.
-template <int BY>
-__device__ __forceinline__ const BatchEntry& batch_entry_shared(const BatchEntry* __restrict__ tab, int n, long long t,
-                                                                BatchEntry& se, int& cached) {
-  const int idx = batch_entry_of(tab, n, t);
-  if (idx != cached) {
-    __syncthreads();  // the previous tile's readers are done with se
-    const int* s = reinterpret_cast<const int*>(tab + idx);
-    int* d = reinterpret_cast<int*>(&se);
-    for (int w = threadIdx.x; w < (int)(sizeof(BatchEntry) / sizeof(int)); w += BY) d[w] = s[w];
-    __syncthreads();
-    cached = idx;
-  }
-  return se;
-}
-
 // f^eq of one site into feq[37] (host or device).
 __host__ __device__ inline void equilibrium(const ShellConsts& c, double rho, double ux, double uy, double T,
                                             double* feq) {

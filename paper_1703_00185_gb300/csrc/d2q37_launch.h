@@ -33,11 +33,13 @@ int launch_init_equilibrium32(float* buf, const double* T, const StepParams& p, 
 // Batched fused step over a table of n lattices (BatchEntry, device memory),
 // tiles of block_y rows; block_y in {64, 128, 256}; grid = number of blocks
 // of the grid-stride loop.  *_blocks_per_sm: resident blocks per SM.
-int launch_batch_fused(const BatchEntry* tab, int n, long long tiles, int parity, int block_y, int grid,
-                       cudaStream_t stream);
+// tile_entry: owning entry of every tile (device, tiles values), or null
+// for a binary search over the table's tile0
+int launch_batch_fused(const BatchEntry* tab, const int* tile_entry, int n, long long tiles, int parity,
+                       int block_y, int grid, cudaStream_t stream);
 int batch_blocks_per_sm(int block_y);
-int launch_batch_fused32(const BatchEntry* tab, int n, long long tiles, int parity, int block_y, int grid,
-                         bool wide_fp64, cudaStream_t stream);
+int launch_batch_fused32(const BatchEntry* tab, const int* tile_entry, int n, long long tiles, int parity,
+                         int block_y, int grid, bool wide_fp64, cudaStream_t stream);
 int batch32_blocks_per_sm(int block_y, bool wide_fp64);
 
 // One population plane between a contiguous FP64 [Lx][Ly] array (f) and the
