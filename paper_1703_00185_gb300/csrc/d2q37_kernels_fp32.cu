@@ -103,6 +103,20 @@ __device__ __forceinline__ Split split_deviation(float v) {
   return {__float_as_int(t1) - __float_as_int(m1), __float_as_int(t2) - __float_as_int(m2)};
 }
 
+// The same split for the two populations of a pair at once, with the
+// packed FP32 instructions of sm_100+ (two lanes per instruction issue;
+// the arithmetic, and so the result, is that of split_deviation).
+__device__ __forceinline__ void split_pair(float vp, float vm, Split& sp, Split& sm) {
+  const float m1 = 6.0f, m2 = 0x1.8p-20f;
+  const float2 v = make_float2(vp, vm);
+  const float2 t1 = __fadd2_rn(v, make_float2(m1, m1));
+  const float2 u = __fadd2_rn(t1, make_float2(-m1, -m1));
+  const float2 r = __ffma2_rn(u, make_float2(-1.0f, -1.0f), v);  // v - u, exact
+  const float2 t2 = __fadd2_rn(r, make_float2(m2, m2));
+  sp = {__float_as_int(t1.x) - __float_as_int(m1), __float_as_int(t2.x) - __float_as_int(m2)};
+  sm = {__float_as_int(t1.y) - __float_as_int(m1), __float_as_int(t2.y) - __float_as_int(m2)};
+}
+
 __device__ __forceinline__ long long join(int hi, int lo) { return (long long)hi * (1LL << 22) + lo; }
 
 __device__ __forceinline__ Sums deviation_sums_wide(const float (&d)[kQ]) {
@@ -155,8 +169,8 @@ __device__ __forceinline__ Sums deviation_sums(const float (&d)[kQ]) {
   int jx_hi = 0, jx_lo = 0, jy_hi = 0, jy_lo = 0;
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
-    const Split vp = split_deviation(d[1 + 2 * p]);
-    const Split vm = split_deviation(d[2 + 2 * p]);
+    Split vp, vm;
+    split_pair(d[1 + 2 * p], d[2 + 2 * p], vp, vm);
     const int k = pair_shell(p);
     sh_hi[k] += vp.hi + vm.hi;
     sh_lo[k] += vp.lo + vm.lo;
@@ -273,7 +287,7 @@ __device__ __forceinline__ void collide_site32(float (&d)[kQ], const StepParams&
   float moved = 0.0f, moved_e = 0.0f;
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
-    float moved_k = 0.0f;
+    float2 moved_k2 = make_float2(0.0f, 0.0f);  // per lane: the +c and the -c populations
     const float ow = p.omega_f * c.w[k];
     const float rC1 = rho_f * fmaf(th_f, c.delta[k], B1);
     const float rC2 = rho_f * fmaf(th_f, c.eps[k], B2);
@@ -284,14 +298,19 @@ __device__ __forceinline__ void collide_site32(float (&d)[kQ], const StepParams&
       const int cx = pair_cx(pr), cy = pair_cy(pr);
       const float a = cx == 0 ? cy * suy : (cy == 0 ? cx * sux : fmaf((float)cx, sux, cy * suy));
       const float b = a * a;
-      const float even = b * fmaf(b, r24, rC2);
-      const float odd = a * fmaf(b, r6, rC1);
-      const float np = fmaf(keep, d[1 + 2 * pr], ow * (G0[k] + even + odd));
-      const float nm = fmaf(keep, d[2 + 2 * pr], ow * (G0[k] + even - odd));
-      moved_k += (np - d[1 + 2 * pr]) + (nm - d[2 + 2 * pr]);
-      d[1 + 2 * pr] = np;
-      d[2 + 2 * pr] = nm;
+      // (even, odd) = (b (b/24 + C2), a (b/6 + C1)) rho, in one packed FMA and multiply
+      const float2 eo = __fmul2_rn(make_float2(b, a), __ffma2_rn(make_float2(b, b), make_float2(r24, r6),
+                                                               make_float2(rC2, rC1)));
+      const float ge = G0[k] + eo.x;
+      // (G0 + even + odd, G0 + even - odd), exact sign flips
+      const float2 gpm = __ffma2_rn(make_float2(eo.y, eo.y), make_float2(1.0f, -1.0f), make_float2(ge, ge));
+      const float2 dd = make_float2(d[1 + 2 * pr], d[2 + 2 * pr]);
+      const float2 nn = __ffma2_rn(make_float2(keep, keep), dd, __fmul2_rn(make_float2(ow, ow), gpm));
+      moved_k2 = __fadd2_rn(moved_k2, __ffma2_rn(dd, make_float2(-1.0f, -1.0f), nn));  // += nn - dd
+      d[1 + 2 * pr] = nn.x;
+      d[2 + 2 * pr] = nn.y;
     }
+    const float moved_k = moved_k2.x + moved_k2.y;
     moved += moved_k;
     moved_e = fmaf((float)shell_c2(k), moved_k, moved_e);
   }
