@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip timing the 64-lattice batched forms")
     ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--batched-lattices", type=int, default=64,
+                    help="lattices in the batched form (64 is the workload; fewer make a small profiling case)")
     ap.add_argument("--serving-jobs", type=int, default=40, help="0 skips the serving run")
     ap.add_argument("--serving-budget-gb", type=float, default=96.0)
     ap.add_argument("--serving-steps-per-tick", type=int, default=16)
@@ -274,13 +276,14 @@ def time_form(torch, lbm, a, dev, precision, kernel, steps, seed, dist=None, sam
 
 
 def run_batched(torch, lbm, a, dev):
-    """64 uneven Rayleigh-Taylor lattices advanced together, one launch per
+    """a.batched_lattices (64) uneven Rayleigh-Taylor lattices advanced together, one launch per
     step (graph-replayed), launch shape from the autotuner; FP64 and FP32."""
     from paper_1703_00185_gb300 import workloads
-    jobs = workloads.batched_lattices(1, 64)
+    jobs = workloads.batched_lattices(1, a.batched_lattices)
     sites = sum(j["Lx"] * j["Ly"] for j in jobs)
-    out = {"workload": "64 Rayleigh-Taylor lattices, Lx in {128..1024 step 128}, Ly in {256..2048 step 256}, "
-                       "per-lattice seed and T_bot ~ U(1.2, 1.8) from master seed 1", "sites": sites}
+    out = {"workload": "%d Rayleigh-Taylor lattices, Lx in {128..1024 step 128}, Ly in {256..2048 step 256}, "
+                       "per-lattice seed and T_bot ~ U(1.2, 1.8) from master seed 1" % a.batched_lattices,
+           "sites": sites}
     for prec in ("fp64", "fp32-df"):
         lats = []
         for j in jobs:
