@@ -220,14 +220,22 @@ __device__ __forceinline__ long long to_fx(double v) {
   return hi < 0 ? -r : r;
 }
 
-// g 2^(E - 55) as an FP64 number.  Two ways, chosen at build time
-// (D2Q37_FX_CVT): 0 with integer operations only (round half away from
-// zero), 1 with the FP64 pipe's 64-bit integer conversion (round to nearest
-// even) and the power of two added to the exponent field.
-// On GB300 the FP64 pipe, at 37 % with the integer form, takes the 37
-// conversions per site: 4.12 ms against 4.37 ms per 2048 x 8192 step.
+// g 2^(E - 55) as an FP64 number, two ways: with the FP64 pipe's 64-bit
+// integer conversion (round to nearest even) and the power of two added to
+// the exponent field, or with integer operations only (round half away from
+// zero).  D2Q37_FX_CVT chooses at build time: 1 on the FP64 pipe (on GB300
+// 4.12 ms per 2048 x 8192 step against 4.37 ms for 0, integer; converting
+// half the populations each way was slower still, 4.65 ms at 4 blocks/SM).
 #ifndef D2Q37_FX_CVT
 #define D2Q37_FX_CVT 1
+#endif
+
+#if D2Q37_FX_CVT != 0
+__device__ __forceinline__ double fx_to_double_fp64(long long g, int E) {
+  const double d = (double)g;  // exact up to its one rounding
+  const u64 bits = (u64)__double_as_longlong(d) + ((u64)(long long)(E - kFxOut) << 52);
+  return g ? __longlong_as_double((long long)bits) : 0.0;
+}
 #endif
 
 #if D2Q37_FX_CVT == 0
@@ -240,14 +248,8 @@ __device__ __noinline__ double fx_to_double_small(u64 m, int E, u64 sign) {
   const u64 bits = ((u64)(long long)(1023 + 7 + E - lz) << 52) + mant;
   return __longlong_as_double((long long)(bits | sign));
 }
-#endif
 
-__device__ __forceinline__ double fx_to_double(long long g, int E) {
-#if D2Q37_FX_CVT == 1
-  const double d = (double)g;  // exact up to its one rounding
-  const u64 bits = (u64)__double_as_longlong(d) + ((u64)(long long)(E - kFxOut) << 52);
-  return g ? __longlong_as_double((long long)bits) : 0.0;
-#else
+__device__ __forceinline__ double fx_to_double_int(long long g, int E) {
   const u64 sm = (u64)(g >> 63);
   const u64 sign = sm & 0x8000000000000000ull;
   const u64 m = ((u64)g ^ sm) - sm;  // |g| < 2^63
@@ -261,6 +263,14 @@ __device__ __forceinline__ double fx_to_double(long long g, int E) {
   // the leading one of mant adds 1 to the exponent field (and a carry one more)
   const u64 bits = ((u64)(long long)(1023 + 7 + E - lz) << 52) + mant;
   return __longlong_as_double((long long)(bits | sign));
+}
+#endif
+
+__device__ __forceinline__ double fx_to_double(long long g, int E) {
+#if D2Q37_FX_CVT == 0
+  return fx_to_double_int(g, E);
+#else
+  return fx_to_double_fp64(g, E);
 #endif
 }
 
@@ -283,7 +293,16 @@ __device__ __forceinline__ bool collide_site_fx(double (&f)[kQ], const StepParam
                                                 double uy, double T) {
   const double uby = uy + p.uy_shift;
   const double th = T + p.theta_shift;
-  if (!(rho > 0.0 && rho < 4.0 && fabs(ux) < 0.35 && fabs(uby) < 0.35 && fabs(th) < 1.0)) return false;
+  // rho in (0, 4), |ux|, |uby| < 0.35, |th| < 1 as integer compares of the bit
+  // patterns (ordered like the values for finite positive doubles; NaN fails),
+  // keeping these tests off the FP64 pipe
+  constexpr long long kAbs = 0x7FFFFFFFFFFFFFFFLL;
+  const long long brho = __double_as_longlong(rho);
+  if (!(brho > 0 && brho < 0x4010000000000000LL &&                      // 4.0
+        (__double_as_longlong(ux) & kAbs) < 0x3FD6666666666666LL &&     // 0.35
+        (__double_as_longlong(uby) & kAbs) < 0x3FD6666666666666LL &&
+        (__double_as_longlong(th) & kAbs) < 0x3FF0000000000000LL))      // 1.0
+    return false;
   const long long UX = to_fx<64>(ux), UY = to_fx<64>(uby);  // Q64
   const long long TH = to_fx<62>(th);                        // Q62
   const u64 R = (u64)to_fx<61>(rho);                         // Q61
