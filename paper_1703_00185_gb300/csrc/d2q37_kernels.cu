@@ -245,7 +245,7 @@ __device__ __noinline__ double fx_to_double_small(u64 m, int E, u64 sign) {
   const int lz = __clzll((long long)m);
   const u64 n = m << (lz - 1);  // leading one at bit 62
   const u64 mant = (n + 0x200) >> 10;
-  const u64 bits = ((u64)(long long)(1023 + 7 + E - lz) << 52) + mant;
+  const u64 bits = ((u64)(long long)(1023 + 62 - kFxOut + E - lz) << 52) + mant;
   return __longlong_as_double((long long)(bits | sign));
 }
 
@@ -261,7 +261,7 @@ __device__ __forceinline__ double fx_to_double_int(long long g, int E) {
   const u64 n = m << (lz - 1);
   const u64 mant = (n + 0x200) >> 10;  // 53 bits, 54 when the rounding carries
   // the leading one of mant adds 1 to the exponent field (and a carry one more)
-  const u64 bits = ((u64)(long long)(1023 + 7 + E - lz) << 52) + mant;
+  const u64 bits = ((u64)(long long)(1023 + 62 - kFxOut + E - lz) << 52) + mant;
   return __longlong_as_double((long long)(bits | sign));
 }
 #endif
