@@ -60,6 +60,13 @@ void fill_fixed_consts(StepParams& sp) {
     sp.fx_c24[k] = fixed_u64(q24, q24l, 68);
   }
   sp.fx_s62 = fixed_u64(c.s, 0.0, 62);
+  sp.fx_s63 = fixed_u64(c.s, 0.0, 63);
+  const double s2h = c.s * c.s, s2l = std::fma(c.s, c.s, -s2h);
+  sp.fx_s2_63 = fixed_u64(s2h, s2l, 63);
+  // the shifted-field constants: tau g_y in Q64 and theta_shift in Q60 (signed)
+  sp.fx_on = std::fabs(sp.uy_shift) < 0.35 && sp.theta_shift > -4.0 && sp.theta_shift < 4.0;
+  sp.fx_uy_shift = sp.fx_on ? std::llround(std::ldexp(sp.uy_shift, 64)) : 0;
+  sp.fx_th_shift = sp.fx_on ? std::llround(std::ldexp(sp.theta_shift, 60)) : 0;
 }
 
 void solve_once() {

@@ -104,20 +104,19 @@ __device__ __forceinline__ long long fixed_term(double v, int emax) {
   return hi < 0 ? -r : r;
 }
 
-__device__ __forceinline__ void site_moments(const double (&f)[kQ], double& rho, double& ux, double& uy,
-                                             double& T) {
-  int emax = 0;
+// The exact sums r = sum f, jx, jy = sum c f, e = sum |c|^2 f on the grid
+// 2^(emax - 1075); false for the sites that take the FP64 sums.
+__device__ __forceinline__ bool site_sums(const double (&f)[kQ], long long& r, long long& jx, long long& jy,
+                                          long long& e, int& emax) {
+  emax = 0;
 #pragma unroll
   for (int l = 0; l < kQ; ++l) emax = max(emax, (__double2hiint(f[l]) >> 20) & 0x7FF);
-  if (emax < 64 || emax > 2046) {
-    site_moments_fp64(f, rho, ux, uy, T);
-    return;
-  }
+  if (emax < 64 || emax > 2046) return false;
   long long sh[kShells];
   sh[0] = fixed_term(f[0], emax);
 #pragma unroll
   for (int k = 1; k < kShells; ++k) sh[k] = 0;
-  long long jx = 0, jy = 0;
+  jx = jy = 0;
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
     const long long vp = fixed_term(f[1 + 2 * p], emax);
@@ -127,18 +126,34 @@ __device__ __forceinline__ void site_moments(const double (&f)[kQ], double& rho,
     jx += pair_cx(p) * d;
     jy += pair_cy(p) * d;
   }
-  long long r = sh[0], e = 0;
+  r = sh[0];
+  e = 0;
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
     r += sh[k];
     e += shell_c2(k) * sh[k];
   }
+  return true;
+}
+
+__device__ __forceinline__ void moments_from_sums(long long r, long long jx, long long jy, long long e, int emax,
+                                                  double& rho, double& ux, double& uy, double& T) {
   const double rd = (double)r;
   const double inv = 1.0 / rd;  // the grid scale cancels in u and T
   ux = c_shell.s * (double)jx * inv;
   uy = c_shell.s * (double)jy * inv;
   T = 0.5 * (c_shell.s2 * (double)e * inv - (ux * ux + uy * uy));
   rho = rd * __hiloint2double((emax - 52) << 20, 0);  // 2^(emax - 1075)
+}
+
+__device__ __forceinline__ void site_moments(const double (&f)[kQ], double& rho, double& ux, double& uy,
+                                             double& T) {
+  long long r, jx, jy, e;
+  int emax;
+  if (site_sums(f, r, jx, jy, e, emax))
+    moments_from_sums(r, jx, jy, e, emax, rho, ux, uy, T);
+  else
+    site_moments_fp64(f, rho, ux, uy, T);
 }
 
 // c v for a hop component c in -3..3 given the multiples m = {v, 2v, 3v}.
@@ -286,26 +301,76 @@ __device__ __forceinline__ long long fx_hop_dot(int cx, int cy, const long long 
   return fx_hop_term(cx, mx) + fx_hop_term(cy, my);
 }
 
-// The collision of collide_site below with the equilibrium in fixed point
-// (formats in the comments).  False (f untouched) when the site is outside
-// the fixed-point ranges.
-__device__ __forceinline__ bool collide_site_fx(double (&f)[kQ], const StepParams& p, double rho, double ux,
-                                                double uy, double T) {
-  const double uby = uy + p.uy_shift;
-  const double th = T + p.theta_shift;
-  // rho in (0, 4), |ux|, |uby| < 0.35, |th| < 1 as integer compares of the bit
-  // patterns (ordered like the values for finite positive doubles; NaN fails),
-  // keeping these tests off the FP64 pipe
-  constexpr long long kAbs = 0x7FFFFFFFFFFFFFFFLL;
-  const long long brho = __double_as_longlong(rho);
-  if (!(brho > 0 && brho < 0x4010000000000000LL &&                      // 4.0
-        (__double_as_longlong(ux) & kAbs) < 0x3FD6666666666666LL &&     // 0.35
-        (__double_as_longlong(uby) & kAbs) < 0x3FD6666666666666LL &&
-        (__double_as_longlong(th) & kAbs) < 0x3FF0000000000000LL))      // 1.0
-    return false;
-  const long long UX = to_fx<64>(ux), UY = to_fx<64>(uby);  // Q64
-  const long long TH = to_fx<62>(th);                        // Q62
-  const u64 R = (u64)to_fx<61>(rho);                         // Q61
+// Fixed-point site values: rho (Q61), u_x and u_bar_y = u_y + tau g_y (Q64),
+// theta = T_bar - 1 (Q62).
+struct FxSite {
+  u64 R;
+  long long UX, UY, TH;
+};
+
+// The fixed-point site values straight from the exact moment sums (no FP64
+// arithmetic): with r normalised to rn = r 2^n in [2^63, 2^64), X = 2^126 / rn
+// from a float seed and two Newton steps (about 2^-60 relative), then
+// j / r = (j 2^n) X 2^-126, u = s j / r, 2 T = s^2 e / r - |u|^2 (unshifted u,
+// reading R6), rho = r 2^(emax - 1075).  False when the site is outside the
+// fixed-point ranges (rho in (0, 4), |u_x|, |u_bar_y| < 0.35, |theta| < 1) or
+// its sums do not fit the scaled forms; those sites take the FP64 collision.
+__device__ __forceinline__ bool fx_site_from_sums(long long r, long long jx, long long jy, long long e, int emax,
+                                                  const StepParams& p, FxSite& o) {
+  if (!p.fx_on || r <= 0 || e < 0) return false;
+  const u64 ur = (u64)r;
+  const u64 ajx = jx < 0 ? 0ull - (u64)jx : (u64)jx, ajy = jy < 0 ? 0ull - (u64)jy : (u64)jy;
+  // |j| < r / 2 and e < 3 r keep the scaled sums inside 64 bits (r < 37 2^53)
+  if ((ajx << 1) >= ur || (ajy << 1) >= ur || (u64)e >= ur + ur + ur) return false;
+  const int n = __clzll(r);  // >= 5
+  const u64 rn = ur << n;
+  const unsigned top = (unsigned)(rn >> 40);  // [2^23, 2^24), exactly a float below
+  const unsigned rb = __float_as_uint(__frcp_rn(__int_as_float(0x4B000000 | (int)(top & 0x7FFFFF))));
+  u64 X = (u64)((rb & 0x7FFFFF) | 0x800000) << (((rb >> 23) & 0xFF) - 64);  // 1/top 2^86, Q62 of 2^64/rn
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const u64 pq = __umul64hi(rn, X);          // Q62 of rn X, about 1
+    X = __umul64hi(X, (1ull << 63) - pq) << 2;  // X (2 - rn X), Q62; never above 2^64 / rn
+  }
+  const long long qx = mulhi_su((long long)((u64)jx << n), X);  // Q62 of jx / r
+  const long long qy = mulhi_su((long long)((u64)jy << n), X);
+  const long long ux61 = mulhi_su(qx, p.fx_s63);  // Q61 of u_x = s jx / r
+  const long long uy61 = mulhi_su(qy, p.fx_s63);
+  constexpr long long kU = 0x0B33333333333333LL;  // 0.35 2^61
+  if (ux61 >= kU || ux61 <= -kU) return false;
+  const long long UX = (long long)((u64)ux61 << 3);                      // Q64
+  const long long UY0 = (long long)((u64)uy61 << 3);                     // Q64, unshifted
+  const long long UY = UY0 + p.fx_uy_shift;                              // Q64 of u_bar_y
+  if (UY >= 0x5999999999999999LL || UY <= -0x5999999999999999LL) return false;  // 0.35 2^64
+  const u64 aux = UX < 0 ? 0ull - (u64)UX : (u64)UX, auy = UY0 < 0 ? 0ull - (u64)UY0 : (u64)UY0;
+  const u64 er = __umul64hi((u64)e << (n - 2), X);                      // Q60 of e / r (< 3)
+  const u64 s2er = __umul64hi(er, p.fx_s2_63);                           // Q59 of s^2 e / r
+  const u64 q0 = __umul64hi(aux, aux) + __umul64hi(auy, auy);            // Q64 of |u|^2
+  const long long th60 = (long long)s2er - (long long)(q0 >> 5) + p.fx_th_shift;  // Q60 of T + shift
+  if (th60 >= (1LL << 60) || th60 <= -(1LL << 60)) return false;
+  const int sR = emax - 1014;  // rho 2^61 = r 2^sR
+  u64 R;
+  if (sR >= 0) {
+    if (sR >= n) return false;
+    R = ur << sR;
+  } else {
+    const int rs = min(-sR, 63);
+    R = (ur + (1ull << (rs - 1))) >> rs;
+  }
+  if (R == 0 || R >= (1ull << 63)) return false;
+  o.R = R;
+  o.UX = UX;
+  o.UY = UY;
+  o.TH = (long long)((u64)th60 << 2);
+  return true;
+}
+
+// The collision of collide_site_fp64 below with the equilibrium in fixed
+// point (formats in the comments), for a site inside the fixed-point ranges.
+__device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParams& p, const FxSite& fs) {
+  const long long UX = fs.UX, UY = fs.UY;  // Q64
+  const long long TH = fs.TH;              // Q62
+  const u64 R = fs.R;                      // Q61
   const u64 AUX = UX < 0 ? 0ull - (u64)UX : (u64)UX, AUY = UY < 0 ? 0ull - (u64)UY : (u64)UY;
   const u64 q = __umul64hi(AUX, AUX) + __umul64hi(AUY, AUY);  // Q64
   const u64 q2 = __umul64hi(q, q);                            // Q64
@@ -355,17 +420,14 @@ __device__ __forceinline__ bool collide_site_fx(double (&f)[kQ], const StepParam
       f[2 + 2 * pr] = fma(keep, f[2 + 2 * pr], fx_to_double(even - odd, E));
     }
   }
-  return true;
 }
 
 // BGK collision of one site, f <- f - (f - f^eq(rho, u_bar, T_bar)) / tau with
 // u_bar = u + tau g, T_bar = T - tau^2 g^2 / D (Eq. MASTERSHIFT3, Eq. discrete).
 // The equilibrium is evaluated per pair as even +- odd parts with per-shell
 // coefficients (see ShellConsts), pre-scaled by omega rho w_shell.
-__device__ __forceinline__ void collide_site(double (&f)[kQ], const StepParams& p) {
-  double rho, ux, uy, T;
-  site_moments(f, rho, ux, uy, T);
-  if (collide_site_fx(f, p, rho, ux, uy, T)) return;
+__device__ __forceinline__ void collide_site_fp64(double (&f)[kQ], const StepParams& p, double rho, double ux,
+                                                  double uy, double T) {
   const double ubx = ux;
   const double uby = uy + p.uy_shift;
   const double q = ubx * ubx + uby * uby;
@@ -402,6 +464,25 @@ __device__ __forceinline__ void collide_site(double (&f)[kQ], const StepParams& 
       f[2 + 2 * pr] = fma(keep, f[2 + 2 * pr], even - odd);
     }
   }
+}
+
+// One site's collision: moments as exact integer sums, then the fixed-point
+// form inside its ranges, else the FP64 form.
+__device__ __forceinline__ void collide_site(double (&f)[kQ], const StepParams& p) {
+  long long r, jx, jy, e;
+  int emax;
+  FxSite fs;
+  const bool sums = site_sums(f, r, jx, jy, e, emax);
+  if (sums && fx_site_from_sums(r, jx, jy, e, emax, p, fs)) {
+    collide_site_fx(f, p, fs);
+    return;
+  }
+  double rho, ux, uy, T;
+  if (sums)
+    moments_from_sums(r, jx, jy, e, emax, rho, ux, uy, T);
+  else
+    site_moments_fp64(f, rho, ux, uy, T);
+  collide_site_fp64(f, p, rho, ux, uy, T);
 }
 
 // Wall bc for a site of a wall band, applied to its gathered populations:

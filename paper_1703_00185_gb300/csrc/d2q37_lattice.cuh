@@ -142,6 +142,10 @@ struct StepParams {
   unsigned long long fx_ck[kShells], fx_ck2[kShells], fx_ck4[kShells], fx_c6[kShells], fx_c24[kShells];
   int fx_e[kShells];
   unsigned long long fx_s62;  // s 2^62
+  unsigned long long fx_s63, fx_s2_63;  // s 2^63, s^2 2^63
+  long long fx_uy_shift;      // tau g_y 2^64
+  long long fx_th_shift;      // (theta_shift) 2^60 = (-tau^2 g^2 / 2 - 1) 2^60
+  int fx_on;                  // 0: the shifts do not fit the formats, every site takes FP64
 };
 
 // One lattice of a batched launch.  Tiles are one column x by `block_y`
