@@ -35,13 +35,13 @@ BYTES_PER_SITE = {"fp64": 592, "fp32": 296, "fp32-df": 296}
 # 17.15 DADD + 106.06 DMUL + 178.00 DFMA = 301.2 FP64 instructions, 479.2 flop
 # FP64-pipe instructions per site of the fused FP64 kernel (ncu on 2048 x 1024:
 # DFMA + DMUL + DADD + the integer-to-FP64 conversions)
-FP64_PIPE_INST_PER_SITE = 99.6
+FP64_PIPE_INST_PER_SITE = 79.6
 # FP64 pipe peak from unit counts and clocks: 2 FP64 instructions per SM per
 # clock (ncu: ...dfma_pred_on.avg.peak_sustained = 2) x 152 SMs x 2.07 GHz
 FP64_PEAK_GINST = 2 * 152 * 2.07
 # DRAM bytes per fused launch at 2048 x 8192, scaled by sites from the ncu
-# capture of the same kernel on 2048 x 1024 (1257.2 MB per launch there)
-FUSED_TRAFFIC_BYTES_2048x8192 = 1257.2e6 * 8
+# capture of the same kernel on 2048 x 1024 (1257.5 MB per launch there)
+FUSED_TRAFFIC_BYTES_2048x8192 = 1257.5e6 * 8
 # the same for the FP32-storage double-float kernel, from its capture on
 # 2048 x 2048 (1267.2 MB per launch there)
 FUSED32_DF_TRAFFIC_BYTES_2048x8192 = 1267.2e6 * 4
