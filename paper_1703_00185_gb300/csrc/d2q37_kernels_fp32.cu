@@ -48,6 +48,7 @@ struct WideF64 {
   static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
   static __device__ __forceinline__ T mul(T a, float b) { return a * (double)b; }
   static __device__ __forceinline__ T rcp(T a) { return 1.0 / a; }
+  static __device__ __forceinline__ float fixed_to_float(long long v, int e) { return (float)from_fixed(v, e); }
   static __device__ __forceinline__ float tof(T a) { return (float)a; }
   // K0 + x2 (K1 + x2 K2) rounded to float
   static __device__ __forceinline__ float quad(T K0, T K1, T K2, double x2, float, float) {
@@ -65,7 +66,8 @@ struct WideDF {
   static __device__ __forceinline__ T sub(T a, T b) { return df_add_fast(a, df_neg(b)); }
   static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
   static __device__ __forceinline__ T mul(T a, float b) { return df_mul(a, b); }
-  static __device__ __forceinline__ T rcp(T a) { return df_rcp(a); }
+  static __device__ __forceinline__ T rcp(T a) { return df_rcp_fast(a); }
+  static __device__ __forceinline__ float fixed_to_float(long long v, int e) { return float_from_int64(v, e); }
   static __device__ __forceinline__ float tof(T a) { return df_to_float(a); }
   static __device__ __forceinline__ float quad(T K0, T K1, T K2, double, float x2h, float x2l) {
     return df_to_float(df_quad(K0, K1, K2, {x2h, x2l}));
@@ -203,7 +205,7 @@ __device__ __forceinline__ Sums deviation_sums(const float (&d)[kQ]) {
 // Float value of an integer sum on the grid 2^ex.
 template <class W>
 __device__ __forceinline__ float fixed_to_float(long long v, int ex) {
-  return W::tof(W::from_fixed(v, ex));
+  return W::fixed_to_float(v, ex);
 }
 
 // BGK collision of one site in deviation form:
