@@ -216,7 +216,7 @@ void lbm_batch_destroy(lbm_batch_t* b);
  * steps, one batched fused launch per step on cuda_stream, exactly as
  * lbm_batch_step with tiles of 128 rows.  It allocates no device memory and
  * calls no allocating library routine: its tile table lives in a file-scope
- * static device array of LBM_STATIC_BATCH_MAX entries (about 190 KB) that
+ * static device array of LBM_STATIC_BATCH_MAX entries (about 450 KB) that
  * every GPU loading this library holds until the process exits.
  *  - n > LBM_STATIC_BATCH_MAX returns LBM_ETOOBIG and does nothing.
  *  - The first call on a device looks up the array's device address
