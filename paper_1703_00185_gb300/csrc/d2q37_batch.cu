@@ -22,6 +22,8 @@ struct lbm_batch_t {
   std::vector<BatchEntry> host_tab[3];  // per block_y choice (64, 128, 256)
   BatchEntry* dev_tab[3];
   int* dev_tile_entry[3];  // owning entry of every tile
+  bool uniform;            // every lattice has the collision constants of `common` (same tau, g)
+  StepParams common;
   long long tiles[3];
   int block_y;        // 64, 128 or 256
   int blocks_per_sm;  // 0: one block per tile; else a persistent grid of blocks_per_sm x SMs
@@ -57,7 +59,7 @@ int launch(lbm_batch_t* b, int block_y, int blocks_per_sm, int parity) {
   const int grid = (int)grid_of(b, block_y, blocks_per_sm);
   const int n = b->prec == LBM_PRECISION_FP64
                     ? launch_batch_fused(b->dev_tab[s], b->dev_tile_entry[s], b->n, b->tiles[s], parity, block_y,
-                                         grid, b->stream)
+                                         grid, b->uniform ? &b->common : nullptr, b->stream)
                     : launch_batch_fused32(b->dev_tab[s], b->dev_tile_entry[s], b->n, b->tiles[s], parity, block_y, grid,
                                            b->prec == LBM_PRECISION_FP32_FP64, b->stream);
   if (n < 0) return LBM_ECUDA;
@@ -130,6 +132,13 @@ int lbm_batch_create(int n, lbm_t* const* lattices, void* cuda_stream, lbm_batch
   b->stream = (cudaStream_t)cuda_stream;
   b->block_y = 128;
   b->blocks_per_sm = 0;
+  b->common = lattices[0]->sp;
+  b->uniform = true;
+  for (int i = 1; i < n; ++i) {
+    const StepParams& q = lattices[i]->sp;
+    b->uniform = b->uniform && q.omega == b->common.omega && q.uy_shift == b->common.uy_shift &&
+                 q.theta_shift == b->common.theta_shift;
+  }
   // the lattices' own pending work comes first; their halos must mirror the state
   for (int i = 0; i < n && !rc; ++i) {
     rc = check(cudaStreamSynchronize(lattices[i]->stream));

@@ -86,7 +86,7 @@ int lbm_batch_step_static(int n, lbm_t* const* lattices, int steps, void* cuda_s
   for (int t = 0; t < steps; ++t) {
     const int launched =
         prec == LBM_PRECISION_FP64
-            ? launch_batch_fused(dev_tab, nullptr, n, tiles, t & 1, 128, grid, stream)
+            ? launch_batch_fused(dev_tab, nullptr, n, tiles, t & 1, 128, grid, nullptr, stream)
             : launch_batch_fused32(dev_tab, nullptr, n, tiles, t & 1, 128, grid, prec == LBM_PRECISION_FP32_FP64, stream);
     if (launched < 0) return LBM_ECUDA;
   }

@@ -602,8 +602,11 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) collide_kernel
 
 // One site of the fused step: gather (pull), wall bc on the wall bands,
 // collide, store with halo images.
+// p: the lattice (geometry, walls); px: the constants of its collision (tau,
+// g: the fixed-point tables, omega, the field shifts), the same object for a
+// single lattice.
 __device__ __forceinline__ void fused_site(const double* __restrict__ src, double* __restrict__ dst,
-                                           const StepParams& p, int x, int y) {
+                                           const StepParams& p, const StepParams& px, int x, int y) {
   const long long i = site_index(p, x, y);
   double f[kQ];
 #pragma unroll
@@ -618,7 +621,7 @@ __device__ __forceinline__ void fused_site(const double* __restrict__ src, doubl
       if (wall ? (cy < -r) : (cy > r)) f[l] = rho_w * p.fw[wall][l];
     }
   }
-  collide_site(f, p);
+  collide_site(f, px);
   store_site(dst, p, x, y, f);
 }
 
@@ -627,16 +630,20 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(c
   const int x = blockIdx.x;
   const int y = blockIdx.y * kBlockY + threadIdx.x;
   if (y >= p.Ly) return;
-  fused_site(src, dst, p, x, y);
+  fused_site(src, dst, p, p, x, y);
 }
 
 // Many lattices in one launch: block-sized tiles (one column x, BY
 // consecutive y) of every lattice in the table, walked by a grid-stride loop
 // (persistent when the grid is sized to the resident blocks).  Lattice i
 // reads buffer cur_i ^ parity and writes the other one.
-template <int BY>
-__global__ void __launch_bounds__(BY, (D2Q37_BATCH_MIN_BLOCKS * 128) / BY > 0 ? (D2Q37_BATCH_MIN_BLOCKS * 128) / BY : 1) batch_fused_kernel(
-    const BatchEntry* __restrict__ tab, const int* __restrict__ tile_entry, int n, long long tiles, int parity) {
+// UNIFORM: every lattice of the launch shares tau and g, so the collision
+// constants come from the kernel argument `common` (constant bank, like the
+// single-lattice kernel) instead of each lattice's entry.
+template <int BY, bool UNIFORM>
+__global__ void __launch_bounds__(BY, (D2Q37_BATCH_MIN_BLOCKS * 128) / BY > 0 ? (D2Q37_BATCH_MIN_BLOCKS * 128) / BY : 1)
+    batch_fused_kernel(const BatchEntry* __restrict__ tab, const int* __restrict__ tile_entry, int n, long long tiles,
+                       int parity, StepParams common) {
   for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
     // owning lattice: per-tile table when given, else binary search; its
     // parameters are read in place (read-only, cached)
@@ -645,7 +652,8 @@ __global__ void __launch_bounds__(BY, (D2Q37_BATCH_MIN_BLOCKS * 128) / BY > 0 ? 
     const int x = local / e.ytiles;
     const int y = (local - x * e.ytiles) * BY + threadIdx.x;
     const int c = e.cur ^ parity;
-    if (y < e.p.Ly) fused_site((const double*)e.buf[c], (double*)e.buf[c ^ 1], e.p, x, y);
+    if (y < e.p.Ly)
+      fused_site((const double*)e.buf[c], (double*)e.buf[c ^ 1], e.p, UNIFORM ? common : e.p, x, y);
   }
 }
 
@@ -735,24 +743,27 @@ int launch_fused(const double* src, double* dst, const StepParams& p, cudaStream
 
 template <int BY>
 int batch_launch(const BatchEntry* tab, const int* tile_entry, int n, long long tiles, int parity, int grid,
-                 cudaStream_t stream) {
-  batch_fused_kernel<BY><<<grid, BY, 0, stream>>>(tab, tile_entry, n, tiles, parity);
+                 const StepParams* common, cudaStream_t stream) {
+  if (common)
+    batch_fused_kernel<BY, true><<<grid, BY, 0, stream>>>(tab, tile_entry, n, tiles, parity, *common);
+  else
+    batch_fused_kernel<BY, false><<<grid, BY, 0, stream>>>(tab, tile_entry, n, tiles, parity, StepParams{});
   return done(1);
 }
 
 template <int BY>
 int batch_occupancy() {
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_fused_kernel<BY>, BY, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_fused_kernel<BY, true>, BY, 0);
   return b;
 }
 
 int launch_batch_fused(const BatchEntry* tab, const int* tile_entry, int n, long long tiles, int parity,
-                       int block_y, int grid, cudaStream_t stream) {
+                       int block_y, int grid, const StepParams* common, cudaStream_t stream) {
   switch (block_y) {
-    case 64: return batch_launch<64>(tab, tile_entry, n, tiles, parity, grid, stream);
-    case 128: return batch_launch<128>(tab, tile_entry, n, tiles, parity, grid, stream);
-    case 256: return batch_launch<256>(tab, tile_entry, n, tiles, parity, grid, stream);
+    case 64: return batch_launch<64>(tab, tile_entry, n, tiles, parity, grid, common, stream);
+    case 128: return batch_launch<128>(tab, tile_entry, n, tiles, parity, grid, common, stream);
+    case 256: return batch_launch<256>(tab, tile_entry, n, tiles, parity, grid, common, stream);
     default: return -1;
   }
 }

@@ -34,9 +34,11 @@ int launch_init_equilibrium32(float* buf, const double* T, const StepParams& p, 
 // tiles of block_y rows; block_y in {64, 128, 256}; grid = number of blocks
 // of the grid-stride loop.  *_blocks_per_sm: resident blocks per SM.
 // tile_entry: owning entry of every tile (device, tiles values), or null
-// for a binary search over the table's tile0
+// for a binary search over the table's tile0.  common (FP64): when every
+// lattice shares tau and g, a StepParams holding their collision constants
+// (passed as a kernel argument), else null.
 int launch_batch_fused(const BatchEntry* tab, const int* tile_entry, int n, long long tiles, int parity,
-                       int block_y, int grid, cudaStream_t stream);
+                       int block_y, int grid, const StepParams* common, cudaStream_t stream);
 int batch_blocks_per_sm(int block_y);
 int launch_batch_fused32(const BatchEntry* tab, const int* tile_entry, int n, long long tiles, int parity,
                          int block_y, int grid, bool wide_fp64, cudaStream_t stream);

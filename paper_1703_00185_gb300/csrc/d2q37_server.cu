@@ -265,7 +265,7 @@ int lbm_server_tick(lbm_server_t* s, int* steps_done) {
     const int grid = (int)std::min<long long>(tiles[g], 2147483647LL);
     for (int t = 0; t < k; ++t) {
       const int launched = g == LBM_PRECISION_FP64
-                               ? launch_batch_fused(s->dev_tab[g], nullptr, n, tiles[g], t & 1, 128, grid, s->stream[g])
+                               ? launch_batch_fused(s->dev_tab[g], nullptr, n, tiles[g], t & 1, 128, grid, nullptr, s->stream[g])
                                : launch_batch_fused32(s->dev_tab[g], nullptr, n, tiles[g], t & 1, 128, grid,
                                                       g == LBM_PRECISION_FP32_FP64, s->stream[g]);
       if (launched < 0) return LBM_ECUDA;
