@@ -21,10 +21,14 @@ def built():
     lbm.load_library()
 
 
-def make(precision, periodic_last=True):
+def make(precision, periodic_last=True, shared_tau=False):
+    """Lattices of different sizes and wall temperatures; with shared_tau all
+    have tau 0.8 and g0 1e-4 (the FP64 batch then takes the collision
+    constants as one kernel argument), else tau differs per lattice."""
     lats = []
     for i, (Lx, Ly) in enumerate(SIZES):
-        lat = lbm.Lattice(Lx, Ly, T_bot=1.2 + 0.1 * i, tau=0.7 + 0.05 * i, precision=precision, device="cuda:0",
+        tau = 0.8 if shared_tau else 0.7 + 0.05 * i
+        lat = lbm.Lattice(Lx, Ly, T_bot=1.2 + 0.1 * i, tau=tau, precision=precision, device="cuda:0",
                           periodic_y=(periodic_last and i == len(SIZES) - 1))
         lat.init_rayleigh_taylor(10 + i)
         lats.append(lat)
@@ -33,8 +37,9 @@ def make(precision, periodic_last=True):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32-df"])
 @pytest.mark.parametrize("config", [(128, 0), (64, 2), (256, 1)])
-def test_batch_equals_alone(precision, config):
-    alone, batched = make(precision), make(precision)
+@pytest.mark.parametrize("shared_tau", [False, True])
+def test_batch_equals_alone(precision, config, shared_tau):
+    alone, batched = make(precision, shared_tau=shared_tau), make(precision, shared_tau=shared_tau)
     for lat in alone:
         lat.step(7)
     b = lbm.Batch(batched)
