@@ -367,9 +367,9 @@ __device__ __forceinline__ void store_site32(float* __restrict__ dst, const Step
   }
   for (int a = 0; a < nx; ++a)
     for (int b = 0; b < ny; ++b) {
-      const int i = (int)site_index(p, xs[a], ys[b]);  // a plane holds < 2^31 elements
+      float* q = dst + (int)site_index(p, xs[a], ys[b]);  // a plane holds < 2^31 elements
 #pragma unroll
-      for (int l = 0; l < kQ; ++l) (dst + l * p.plane)[i] = d[l];
+      for (int l = 0; l < kQ; ++l) q[l * p.plane] = d[l];
     }
 }
 
@@ -438,11 +438,12 @@ __global__ void __launch_bounds__(256) wrap32_kernel(float* __restrict__ buf, St
 template <class W>
 __device__ __forceinline__ void fused_site32(const float* __restrict__ src, float* __restrict__ dst,
                                              const StepParams& p, int x, int y) {
-  // 64-bit plane base (uniform across the block) plus a 32-bit offset
-  const int i = (int)site_index(p, x, y);
+  // the site's pointer once per thread; each population at an offset that is
+  // the same for the whole block (l plane - cx NY - cy)
+  const float* q = src + (int)site_index(p, x, y);
   float d[kQ];
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) d[l] = (src + l * p.plane)[i - vel_cx(l) * p.NY - vel_cy(l)];
+  for (int l = 0; l < kQ; ++l) d[l] = q[l * p.plane - vel_cx(l) * p.NY - vel_cy(l)];
   if (!p.periodic_y && (y < 3 || y >= p.Ly - 3)) {
     const int wall = y >= p.Ly - 3;
     const int r = wall ? p.Ly - 1 - y : y;
