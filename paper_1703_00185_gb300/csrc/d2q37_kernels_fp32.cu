@@ -25,10 +25,11 @@ namespace {
 constexpr int kBlockY = 128;
 
 // Resident blocks of 128 threads per SM requested for the FP32 site kernels:
-// 5 caps registers at 96 (16 bytes spilled) and gives 20 warps per SM; on
-// GB300 that ran the fused kernel at 17.1 G sites/s against 15.1 with 4.
+// 6 caps registers at 80 (20 bytes of spills per thread) and gives 24 warps
+// per SM to hide the memory latency; on GB300 the 2048 x 8192 fused step ran
+// at 19.9 G sites/s against 19.5 with 5 (96 registers) and 19.8 with 7.
 #ifndef D2Q37_FP32_MIN_BLOCKS
-#define D2Q37_FP32_MIN_BLOCKS 5
+#define D2Q37_FP32_MIN_BLOCKS 6
 #endif
 
 __device__ __forceinline__ long long site_index(const StepParams& p, int x, int y) {
