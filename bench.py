@@ -39,6 +39,11 @@ FP64_PIPE_INST_PER_SITE = 79.6
 # FP64 pipe peak from unit counts and clocks: 2 FP64 instructions per SM per
 # clock (ncu: ...dfma_pred_on.avg.peak_sustained = 2) x 152 SMs x 2.07 GHz
 FP64_PEAK_GINST = 2 * 152 * 2.07
+# FP64 flops of one site collision as the oracle writes the method out (its
+# counting build, oracle/flop_count.cpp: every operation, and those without an
+# operand of exactly 0 or +-1); tests/test_oracle_flops.py keeps these equal
+ORACLE_FLOPS_PER_SITE = 42640
+ORACLE_NONTRIVIAL_FLOPS_PER_SITE = 17477
 # DRAM bytes per fused launch at 2048 x 8192, scaled by sites from the ncu
 # capture of the same kernel on 2048 x 1024 (1257.5 MB per launch there)
 FUSED_TRAFFIC_BYTES_2048x8192 = 1257.5e6 * 8
@@ -231,6 +236,15 @@ def roofline_of(kind, avg_s, sites, precision, traffic=None):
          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
          "algorithmic_bytes_per_launch": nbytes}
     if precision == "fp64" and kind in ("fused", "collide"):
+        # the roofline of the survey's formula, min(HBM / bytes, FP64 peak / flops),
+        # with the oracle's flop count: this step does not spend those flops
+        # (integer moments, fixed-point equilibrium), so the HBM one binds
+        peak_flops = 2 * FP64_PEAK_GINST * 1e9
+        r["oracle_flops"] = {"flops_per_site": ORACLE_FLOPS_PER_SITE,
+                             "nontrivial_flops_per_site": ORACLE_NONTRIVIAL_FLOPS_PER_SITE,
+                             "fp64_peak_tflops": round(peak_flops / 1e12, 3),
+                             "flop_roofline_gsites_per_s": round(peak_flops / ORACLE_FLOPS_PER_SITE / 1e9, 4),
+                             "achieved_gsites_per_s": round(sites / avg_s / 1e9, 4)}
         ginst = FP64_PIPE_INST_PER_SITE * sites / avg_s / 1e9
         r["fp64_pipe"] = {"inst_per_site": FP64_PIPE_INST_PER_SITE, "achieved": round(ginst, 2),
                           "peak": round(FP64_PEAK_GINST, 2), "unit": "G FP64-pipe instructions/s",

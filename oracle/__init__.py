@@ -48,6 +48,41 @@ def build(force=False):
     return _LIB
 
 
+_FLOP_SRC = os.path.join(_HERE, "flop_count.cpp")
+_FLOP_LIB = os.path.join(_LIB_DIR, "liboracle_d2q37_flops.so")
+
+
+def build_flop_counter(force=False):
+    """Compile the counting build (g++); returns the library path."""
+    if force or not os.path.exists(_FLOP_LIB) or \
+            os.path.getmtime(_FLOP_LIB) < max(os.path.getmtime(_FLOP_SRC), os.path.getmtime(_SRC)):
+        os.makedirs(_LIB_DIR, exist_ok=True)
+        tmp = _FLOP_LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fpermissive",
+                               "-w", "-fPIC", "-shared", "-D_DEFAULT_SOURCE", "-o", tmp, _FLOP_SRC, "-lm"])
+        os.replace(tmp, _FLOP_LIB)
+    return _FLOP_LIB
+
+
+def collide_flops_per_site(nontrivial=False):
+    """FP64 operations the oracle performs for one site collision (moments,
+    shifted fields, the equilibrium as the full Hermite tensor contraction,
+    relaxation), counted by compiling its source with a counting number type
+    (oracle/flop_count.cpp, g++).  nontrivial=True leaves out operations with
+    an operand of exactly 0 or +-1 (the Kronecker factors of the tensor form)."""
+    lib = ctypes.CDLL(build_flop_counter())
+    lib.orc_count_setup.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.orc_count_setup.restype = ctypes.c_int
+    lib.orc_count_collide_site.argtypes = [ctypes.c_int]
+    lib.orc_count_collide_site.restype = ctypes.c_longlong
+    s, w = scale_and_weights()
+    cx, cy = velocity_set()
+    c2 = (np.asarray(cx) ** 2 + np.asarray(cy) ** 2).tolist()
+    w_shell = np.ascontiguousarray([float(np.asarray(w)[c2.index(k)]) for k in sorted(set(c2))])
+    lib.orc_count_setup(float(s), w_shell.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return int(lib.orc_count_collide_site(1 if nontrivial else 0))
+
+
 def _load():
     global _lib
     if _lib is not None:
