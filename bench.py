@@ -185,11 +185,26 @@ def oracle_mlups(Lx, Ly, seconds, max_steps=None):
 
 
 def cpu_baseline(a):
+    import oracle
     Ly = max(6, a.Ly // 8)
     v, steps, el, cores = oracle_mlups(a.Lx, Ly, a.cpu_seconds)
-    return {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d full oracle steps (pbc+propagate+bc+collide, FP64) of a %dx%d Rayleigh-Taylor lattice "
-                      "(1/8 of the %dx%d workload's rows), %.1f s" % (steps, a.Lx, Ly, a.Lx, a.Ly, el)}
+    out = {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%d full oracle steps (pbc+propagate+bc+collide, FP64) of a %dx%d Rayleigh-Taylor lattice "
+                     "(1/8 of the %dx%d workload's rows), %.1f s" % (steps, a.Lx, Ly, a.Lx, a.Ly, el)}
+    # the same on one core, and the 256 x 128 parity case on all cores and on one,
+    # each a bounded sample (a few seconds)
+    c1 = {}
+    for n in (cores, 1):
+        oracle.set_threads(n)
+        v1, s1, e1, _ = oracle_mlups(256, 128, min(a.cpu_seconds, 3.0), max_steps=100)
+        c1["ms_per_step_%d_cores" % n] = round(e1 / s1 * 1e3, 3)
+        if n == 1:
+            vs, ss, es, _ = oracle_mlups(a.Lx, max(6, a.Ly // 512), min(a.cpu_seconds, 3.0))
+            out["single_core"] = {"value": round(vs, 4), "unit": UNIT, "sample": "%d steps of a %dx%d strip, %.1f s"
+                                  % (ss, a.Lx, max(6, a.Ly // 512), es)}
+    oracle.set_threads(cores)
+    out["c1_256x128"] = c1
+    return out
 
 
 def run_reference(a):

@@ -95,6 +95,7 @@ def _load():
     lib.orc_velocity_set.argtypes = [ip, ip]
     lib.orc_weights.argtypes = [dp]
     lib.orc_threads.restype = ctypes.c_int
+    lib.orc_set_threads.argtypes = [ctypes.c_int]
     lib.orc_equilibrium.argtypes = [ctypes.c_double] * 4 + [dp]
     lib.orc_site_moments.argtypes = [dp, dp, dp, dp, dp]
     lib.orc_collide_site.argtypes = [dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
@@ -144,6 +145,11 @@ def scale_and_weights():
 
 def threads():
     return _load().orc_threads()
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's site loops (the results do not change)."""
+    _load().orc_set_threads(int(n))
 
 
 def equilibrium(rho, ux, uy, T):

@@ -102,6 +102,16 @@ int orc_threads(void) {
 #endif
 }
 
+/* Threads of the site loops from here on (n >= 1); the arithmetic does not
+ * depend on it. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------- equilibrium */
 
 static double kron(int i, int j) { return i == j ? 1.0 : 0.0; }
