@@ -304,6 +304,31 @@ def time_form(torch, lbm, a, dev, precision, kernel, steps, seed, dist=None, sam
     return lat, ms, launches, kt, clocks
 
 
+def separate_form(torch, lbm, a, dev):
+    """The FP64 step as separate kernels (pbc, propagate, bc, collide) on the
+    same workload: the propagate moves 592 B/site and the in-place collide
+    another 592, so the schedule moves 1184 B/site; the HBM fraction is given
+    against both 592 (the fused step's bytes) and 1184."""
+    steps = max(1, min(a.steps, 100))
+    lat, ms, launches, kt, _ = time_form(torch, lbm, a, dev, "fp64", "separate", steps, 1)
+    lat.close()
+    sites = a.Lx * a.Ly
+    peak = measured_peaks().get("hbm_gbs")
+    s_per_step = ms * 1e-3 / steps
+    out = {"value": round(sites / s_per_step / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms / steps, 4),
+           "steps": steps, "gpu_launches": launches,
+           "kernel_ms_per_launch": {k: round(v[0] / v[1], 4) for k, v in kt.items() if v[1]},
+           "hbm": {"peak_gbs": peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
+    for nbytes in (592, 1184):
+        gbs = nbytes * sites / s_per_step / 1e9
+        out["hbm"]["achieved_gbs_at_%d_B_per_site" % nbytes] = round(gbs, 1)
+        out["hbm"]["frac_at_%d_B_per_site" % nbytes] = round(gbs / peak, 4) if peak else None
+    if "propagate" in kt and kt["propagate"][1]:
+        gbs = 592 * sites / (kt["propagate"][0] / kt["propagate"][1] * 1e-3) / 1e9
+        out["propagate_kernel"] = {"achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4) if peak else None}
+    return out
+
+
 def run_batched(torch, lbm, a, dev):
     """a.batched_lattices (64) uneven Rayleigh-Taylor lattices advanced together, one launch per
     step (graph-replayed), launch shape from the autotuner; FP64 and FP32."""
@@ -437,6 +462,8 @@ def run_ours(a):
                            "rel_l2_vs_fp64_after_%d_steps" % a.accuracy_steps:
                                {"rho": errs[0], "u": errs[1], "T": errs[2]},
                            "gpu_launches": fl}
+    separate = separate_form(torch, lbm, a, dev) if (a.precision_forms and a.precision == "fp64" and
+                                                     a.kernel == "fused") else None
     batched = run_batched(torch, lbm, a, dev) if (a.batched and a.precision == "fp64") else None
     serving_summary = run_serving(a, dev) if (a.serving_jobs > 0 and a.precision == "fp64") else None
     if rank == 0:
@@ -451,7 +478,7 @@ def run_ours(a):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "kernel_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]}, "clocks": clocks,
-                "precision_forms": forms or None, "batched_forms": batched, "serving": serving_summary}
+                "precision_forms": forms or None, "separate_form": separate, "batched_forms": batched, "serving": serving_summary}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
