@@ -378,6 +378,10 @@ def run_serving(a, dev):
     trace = workloads.serving_trace(1, rate=50.0, n_jobs=a.serving_jobs)
     runs["rate50_full_size"] = serving.run_trace(trace, budget, a.serving_steps_per_tick, dev,
                                                  time_limit=a.serving_time_limit)
+    # full-size jobs at a rate the GPU sustains (about 1.4e9 site updates per job)
+    trace = workloads.serving_trace(3, rate=2.0, n_jobs=a.serving_jobs)
+    runs["rate2_full_size"] = serving.run_trace(trace, budget, a.serving_steps_per_tick, dev,
+                                                time_limit=a.serving_time_limit)
     for rate in (20.0, 5.0):
         trace = workloads.serving_trace(2, rate=rate, n_jobs=a.serving_jobs, size_scale=0.25)
         runs["rate%g_quarter_size" % rate] = serving.run_trace(trace, budget, a.serving_steps_per_tick, dev,
