@@ -263,9 +263,19 @@ int lbm_server_tick(lbm_server_t* s, int* steps_done) {
     const int n = (int)tab[g].size();
     if (!n || k == 0) continue;
     const int grid = (int)std::min<long long>(tiles[g], 2147483647LL);
+    // FP64 jobs that all share tau and g: their collision constants as one
+    // kernel argument (see launch_batch_fused)
+    bool uniform = true;
+    for (int i = 1; i < n && uniform; ++i) {
+      const StepParams& a = tab[g][0].p;
+      const StepParams& b = tab[g][i].p;
+      uniform = a.omega == b.omega && a.uy_shift == b.uy_shift && a.theta_shift == b.theta_shift;
+    }
+    const StepParams* common = uniform ? &tab[g][0].p : nullptr;
     for (int t = 0; t < k; ++t) {
       const int launched = g == LBM_PRECISION_FP64
-                               ? launch_batch_fused(s->dev_tab[g], nullptr, n, tiles[g], t & 1, 128, grid, nullptr, s->stream[g])
+                               ? launch_batch_fused(s->dev_tab[g], nullptr, n, tiles[g], t & 1, 128, grid, common,
+                                                    s->stream[g])
                                : launch_batch_fused32(s->dev_tab[g], nullptr, n, tiles[g], t & 1, 128, grid,
                                                       g == LBM_PRECISION_FP32_FP64, s->stream[g]);
       if (launched < 0) return LBM_ECUDA;
