@@ -98,19 +98,23 @@ __device__ __forceinline__ long long fixed_term(double v, int emax) {
   const int hi = __double2hiint(v);
   const unsigned lo = (unsigned)__double2loint(v);
   const int e = (hi >> 20) & 0x7FF;
-  const long long mant = ((long long)((hi & 0xFFFFF) | (e ? 0x100000 : 0)) << 32) | lo;
-  const int sh = min(emax - max(e, 1), 62);
-  const long long r = sh ? (mant + (1LL << (sh - 1))) >> sh : mant;  // round half up
-  return hi < 0 ? -r : r;
+  // the implicit one is set for zero and subnormal inputs too: with emax >= 64
+  // their shift is the full 62 and they round to 0, as they should
+  const long long mant = ((long long)((hi & 0xFFFFF) | 0x100000) << 32) | lo;
+  const int sh = min(emax - e, 62);
+  const long long r = (((mant << 1) >> sh) + 1) >> 1;  // mant 2^-sh rounded half up
+  const long long s = hi >> 31;                       // 0 or -1
+  return (r ^ s) - s;
 }
 
 // The exact sums r = sum f, jx, jy = sum c f, e = sum |c|^2 f on the grid
 // 2^(emax - 1075); false for the sites that take the FP64 sums.
 __device__ __forceinline__ bool site_sums(const double (&f)[kQ], long long& r, long long& jx, long long& jy,
                                           long long& e, int& emax) {
-  emax = 0;
+  int hmax = 0;  // the largest |high word|: its exponent field is the largest exponent
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) emax = max(emax, (__double2hiint(f[l]) >> 20) & 0x7FF);
+  for (int l = 0; l < kQ; ++l) hmax = max(hmax, __double2hiint(f[l]) & 0x7FFFFFFF);
+  emax = hmax >> 20;
   if (emax < 64 || emax > 2046) return false;
   long long sh[kShells];
   sh[0] = fixed_term(f[0], emax);
