@@ -201,7 +201,7 @@ using u64 = unsigned long long;
 
 // floor(x y 2^-64) for signed x, unsigned y
 __device__ __forceinline__ long long mulhi_su(long long x, u64 y) {
-  return (long long)(__umul64hi((u64)x, y) - (x < 0 ? y : 0ull));
+  return (long long)(__umul64hi((u64)x, y) - (y & (u64)(x >> 63)));  // x >> 63: 0 or all ones
 }
 
 // round(x y 2^-64) (half up) for signed x, unsigned y.  Used where a floor's
@@ -413,13 +413,14 @@ __device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParam
     for (int pr = 0; pr < kPairs; ++pr) {
       if (pair_shell(pr) != k) continue;
       const long long a = fx_hop_dot(pair_cx(pr), pair_cy(pr), mx, my);  // Q62
-      const u64 A = a < 0 ? 0ull - (u64)a : (u64)a;
+      const long long sa = a >> 63;                                      // 0 or -1
+      const u64 A = (u64)((a ^ sa) - sa);
       const u64 b = __umul64hi(A, A);                                    // Q60
       const long long t = R2 + (long long)(__umul64hi(b, R4) >> 2);     // Q59
       const long long even = R0 + mulhi_su(t, b);                        // Q55
       const long long s = R1 + (long long)(__umul64hi(b, R3) >> 2);     // Q57
       const long long oa = mulhi_su_rn(s, A);                            // Q55: |a| (R1 + b R3)
-      const long long odd = a < 0 ? -oa : oa;
+      const long long odd = (oa ^ sa) - sa;                              // the sign of a
       f[1 + 2 * pr] = fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E));
       f[2 + 2 * pr] = fma(keep, f[2 + 2 * pr], fx_to_double(even - odd, E));
     }
@@ -518,6 +519,12 @@ __device__ __forceinline__ double wall_density(const double* __restrict__ src, c
 // stores are divergence-free except on periodic y edges.
 __device__ __forceinline__ void store_site(double* __restrict__ dst, const StepParams& p, int x, int y,
                                            const double (&f)[kQ]) {
+  if (x >= kHx && x < p.Lx - kHx && (!p.periodic_y || (y >= kHx && y < p.Ly - kHx))) {
+    const long long i = site_index(p, x, y);  // no halo image: the common case
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) dst[l * p.plane + i] = f[l];
+    return;
+  }
   int xs[3] = {x, 0, 0}, ys[3] = {y, 0, 0};
   int nx = 1, ny = 1;
   if (x < kHx) xs[nx++] = x + p.Lx;
