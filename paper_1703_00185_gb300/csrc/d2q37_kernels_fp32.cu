@@ -358,6 +358,12 @@ __device__ __forceinline__ void fields_of_site32(const float (&d)[kQ], double& r
 // Halo images as in the FP64 store_site.
 __device__ __forceinline__ void store_site32(float* __restrict__ dst, const StepParams& p, int x, int y,
                                              const float (&d)[kQ]) {
+  if (x >= kHx && x < p.Lx - kHx && (!p.periodic_y || (y >= kHx && y < p.Ly - kHx))) {
+    float* q = dst + (int)site_index(p, x, y);  // no halo image: the common case
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) q[l * p.plane] = d[l];
+    return;
+  }
   int xs[3] = {x, 0, 0}, ys[3] = {y, 0, 0};
   int nx = 1, ny = 1;
   if (x < kHx) xs[nx++] = x + p.Lx;
