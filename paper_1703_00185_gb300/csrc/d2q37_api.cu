@@ -51,13 +51,16 @@ void fill_fixed_consts(StepParams& sp) {
     // c x2 and c x2^2 in double-double
     const double p1h = ch * x2h, p1l = std::fma(ch, x2h, -p1h) + (cl * x2h + ch * x2l);
     const double p2h = p1h * x2h, p2l = std::fma(p1h, x2h, -p2h) + (p1l * x2h + p1h * x2l);
-    sp.fx_ck[k] = fixed_u64(ch, cl, 64);
-    sp.fx_ck2[k] = fixed_u64(p1h, p1l, 60);
-    sp.fx_ck4[k] = fixed_u64(p2h, p2l, 56);
+    sp.fx_c60[k] = fixed_u64(ch, cl, 60);
+    sp.fx_c62[k] = fixed_u64(ch, cl, 62);
+    sp.fx_c64[k] = fixed_u64(ch, cl, 64);
+    sp.fx_cx2_59[k] = fixed_u64(p1h, p1l, 59);
+    sp.fx_cx2_60[k] = fixed_u64(p1h, p1l, 60);
+    sp.fx_cx4_55[k] = fixed_u64(p2h, p2l, 55);
     const double q6 = ch / 6.0, q6l = (std::fma(-q6, 6.0, ch) + cl) / 6.0;
     const double q24 = ch / 24.0, q24l = (std::fma(-q24, 24.0, ch) + cl) / 24.0;
-    sp.fx_c6[k] = fixed_u64(q6, q6l, 66);
-    sp.fx_c24[k] = fixed_u64(q24, q24l, 68);
+    sp.fx_c6[k] = fixed_u64(q6, q6l, 64);
+    sp.fx_c24[k] = fixed_u64(q24, q24l, 66);
   }
   sp.fx_s62 = fixed_u64(c.s, 0.0, 62);
   sp.fx_s63 = fixed_u64(c.s, 0.0, 63);

@@ -398,16 +398,15 @@ __device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParam
   const long long mx[3] = {SX, SX + SX, SX + SX + SX};                // Q62
   const long long my[3] = {SY, SY + SY, SY + SY + SY};
   const double keep = p.one_minus_omega;
-  f[0] = fma(keep, f[0], fx_to_double(mulhi_su(K0, p.fx_ck[0]) >> 4, p.fx_e[0]));  // x2 = 0
+  f[0] = fma(keep, f[0], fx_to_double(mulhi_su(K0, p.fx_c60[0]), p.fx_e[0]));  // x2 = 0
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
-    const u64 ck = p.fx_ck[k], ck2 = p.fx_ck2[k];
-    const long long R0 = (mulhi_su(K0, ck) >> 4) + (mulhi_su(K1, ck2) >> 1) +
-                         ((long long)__umul64hi(K2, p.fx_ck4[k]) >> 1);                // Q55
-    const long long R1 = (mulhi_su(L0, ck) >> 2) + (mulhi_su(L1, ck2) >> 1);          // Q57
-    const long long R2 = mulhi_su(M0, ck) + mulhi_su(M1, ck2);                        // Q59
-    const u64 R3 = __umul64hi(R, p.fx_c6[k]);                                         // Q63
-    const u64 R4 = __umul64hi(R, p.fx_c24[k]);                                        // Q65
+    const long long R0 = mulhi_su(K0, p.fx_c60[k]) + mulhi_su(K1, p.fx_cx2_59[k]) +
+                         (long long)__umul64hi(K2, p.fx_cx4_55[k]);                   // Q55
+    const long long R1 = mulhi_su(L0, p.fx_c62[k]) + mulhi_su(L1, p.fx_cx2_59[k]);    // Q57
+    const long long R2 = mulhi_su(M0, p.fx_c64[k]) + mulhi_su(M1, p.fx_cx2_60[k]);    // Q59
+    const u64 R3 = __umul64hi(R, p.fx_c6[k]);                                         // Q61
+    const u64 R4 = __umul64hi(R, p.fx_c24[k]);                                        // Q63
     const int E = p.fx_e[k];
 #pragma unroll
     for (int pr = 0; pr < kPairs; ++pr) {
@@ -416,9 +415,9 @@ __device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParam
       const long long sa = a >> 63;                                      // 0 or -1
       const u64 A = (u64)((a ^ sa) - sa);
       const u64 b = __umul64hi(A, A);                                    // Q60
-      const long long t = R2 + (long long)(__umul64hi(b, R4) >> 2);     // Q59
+      const long long t = R2 + (long long)__umul64hi(b, R4);            // Q59
       const long long even = R0 + mulhi_su(t, b);                        // Q55
-      const long long s = R1 + (long long)(__umul64hi(b, R3) >> 2);     // Q57
+      const long long s = R1 + (long long)__umul64hi(b, R3);            // Q57
       const long long oa = mulhi_su_rn(s, A);                            // Q55: |a| (R1 + b R3)
       const long long odd = (oa ^ sa) - sa;                              // the sign of a
       f[1 + 2 * pr] = fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E));

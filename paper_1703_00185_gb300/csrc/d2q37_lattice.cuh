@@ -137,9 +137,13 @@ struct StepParams {
   float wall_e32[2][2];   // (hi, lo): sum_M fwmw32 - sum_O w + sum_M w (M missing, O leaving pairs)
   float wall_inv32[2][2]; // (hi, lo): 1 / sum_M fw32
   // Fixed-point equilibrium constants of the FP64 step: per shell k,
-  // omega w_k = c_k 2^fx_e[k] with c_k in [0.5, 1); as unsigned integers
-  // c 2^64, c x2 2^60, c x2^2 2^56, (c/6) 2^66, (c/24) 2^68 (x2 = s^2 |c_l|^2).
-  unsigned long long fx_ck[kShells], fx_ck2[kShells], fx_ck4[kShells], fx_c6[kShells], fx_c24[kShells];
+  // omega w_k = c_k 2^fx_e[k] with c_k in [0.5, 1); as unsigned integers, each
+  // at the scale that puts its product straight into the format it feeds:
+  // c 2^60, 2^62, 2^64; c x2 2^59, 2^60; c x2^2 2^55; (c/6) 2^64; (c/24) 2^66
+  // (x2 = s^2 |c_l|^2).
+  unsigned long long fx_c60[kShells], fx_c62[kShells], fx_c64[kShells];
+  unsigned long long fx_cx2_59[kShells], fx_cx2_60[kShells], fx_cx4_55[kShells];
+  unsigned long long fx_c6[kShells], fx_c24[kShells];
   int fx_e[kShells];
   unsigned long long fx_s62;  // s 2^62
   unsigned long long fx_s63, fx_s2_63;  // s 2^63, s^2 2^63

@@ -53,8 +53,9 @@ def shell_consts(s, c2, w, omega):
     cw = Fr(omega) * Fr(w)
     E = math.frexp(float(cw))[1]
     c = cw / Fr(2) ** E
-    return dict(E=E, ck=round(c * 2**64), ck2=round(c * x2 * 2**60), ck4=round(c * x2 * x2 * 2**56),
-                c6=round(c / 6 * 2**66), c24=round(c / 24 * 2**68))
+    return dict(E=E, c60=round(c * 2**60), c62=round(c * 2**62), c64=round(c * 2**64),
+                cx2_59=round(c * x2 * 2**59), cx2_60=round(c * x2 * 2**60), cx4_55=round(c * x2 * x2 * 2**55),
+                c6=round(c / 6 * 2**64), c24=round(c / 24 * 2**66))
 
 
 PAIRS = [(1, 0), (0, 1), (1, 1), (1, -1), (2, 0), (0, 2), (2, 1), (2, -1), (1, 2), (1, -2), (2, 2), (2, -2),
@@ -83,9 +84,9 @@ def equilibrium_fixed(s, shells, wk, R, UX, UY, TH, omega):
     out = {}
     for k, c2 in enumerate(shells):
         C = shell_consts(s, c2, wk[k], omega)
-        R0 = fits((mulhi_su(K0, C["ck"]) >> 4) + (mulhi_su(K1, C["ck2"]) >> 1) + (umulhi(K2, C["ck4"]) >> 1), "R0")
-        R1 = fits((mulhi_su(L0, C["ck"]) >> 2) + (mulhi_su(rth, C["ck2"]) >> 1), "R1")
-        R2 = fits(mulhi_su(M0, C["ck"]) + mulhi_su(rth, C["ck2"]), "R2")
+        R0 = fits(mulhi_su(K0, C["c60"]) + mulhi_su(K1, C["cx2_59"]) + umulhi(K2, C["cx4_55"]), "R0")
+        R1 = fits(mulhi_su(L0, C["c62"]) + mulhi_su(rth, C["cx2_59"]), "R1")
+        R2 = fits(mulhi_su(M0, C["c64"]) + mulhi_su(rth, C["cx2_60"]), "R2")
         R3 = fits(umulhi(R, C["c6"]), "R3")
         R4 = fits(umulhi(R, C["c24"]), "R4")
         if c2 == 0:
@@ -97,9 +98,9 @@ def equilibrium_fixed(s, shells, wk, R, UX, UY, TH, omega):
             a = fits(cx * SX + cy * SY, "a")
             A = abs(a)
             b = umulhi(A, A)
-            t = fits(R2 + (umulhi(b, R4) >> 2), "t")
+            t = fits(R2 + umulhi(b, R4), "t")
             even = fits(R0 + mulhi_su(t, b), "even")
-            sv = fits(R1 + (umulhi(b, R3) >> 2), "s")
+            sv = fits(R1 + umulhi(b, R3), "s")
             oa = (sv * A + (1 << 63)) >> 64  # rounded to nearest
             odd = -oa if a < 0 else oa
             out[(cx, cy)] = Fr(fits(even + odd, "G+")) * Fr(2) ** (C["E"] - 55)
