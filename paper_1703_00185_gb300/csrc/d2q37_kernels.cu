@@ -179,8 +179,8 @@ __device__ __forceinline__ double hop_dot(int cx, int cy, const double (&mx)[3],
 // pipes.  So the equilibrium of the FP64 step is evaluated in fixed point:
 // each quantity is an int64 scaled by its own power of two ("Qn": v 2^-n),
 // chosen from its range so that every product is the high word of a 128-bit
-// product (floor rounding) and keeps 2^-55 or better absolute precision on
-// the order-1 quantities; exact integer sums remove the cancellation that
+// product and keeps 2^-55 or better absolute precision on the order-1
+// quantities; exact integer sums remove the cancellation that
 // limits the FP64 form near T = 0.5 for the outer shells.  Per population
 // the result is turned into an FP64 number with integer operations and
 // relaxed with one FP64 FMA.  The shell factor omega w_k is carried as
@@ -195,6 +195,18 @@ __device__ __forceinline__ double hop_dot(int cx, int cy, const double (&mx)[3],
 //   R0 = c (K0 + x2 K1 + x2^2 K2),  R1 = c (L0 + x2 L1),  R2 = c (M0 + x2 M1),
 //   R3 = c rho / 6,  R4 = c rho / 24,
 // and per pair even = R0 + b (R2 + b R4), odd = a (R1 + b R3), b = a^2.
+// The site values' products are exact high words (floor).  The per-shell
+// products (9 per shell) and the even part's per-pair products (b, t, the
+// even product, and the one of s) are umulhi_t, three multiply-adds instead
+// of four, with integer corrections folded into per-shell constants.  A
+// signed site value x meets the unsigned shell constants as x + 2^63 (its sign
+// bit flipped): x y 2^-64 = (x + 2^63) y 2^-64 - y / 2, and the y / 2 terms
+// and the corrections of a shell are one constant subtracted from R0, R1 and
+// R2 (fx_d0, fx_d1, fx_d2).  K0 > 0.74 rho inside the ranges and needs no
+// shift.  The corrections make the equilibrium's mass bias +1.4e-17 per
+// collision relative to omega rho (the floors of exact products: -7.6e-17).
+// The odd part keeps an exact, rounded product: a bias there acts on the
+// momentum the same way every step.
 constexpr int kFxOut = 55;  // format of R0 and of the results G = even +- odd
 
 using u64 = unsigned long long;
@@ -204,13 +216,32 @@ __device__ __forceinline__ long long mulhi_su(long long x, u64 y) {
   return (long long)(__umul64hi((u64)x, y) - (y & (u64)(x >> 63)));  // x >> 63: 0 or all ones
 }
 
-// round(x y 2^-64) (half up) for signed x, unsigned y.  Used where a floor's
-// bias would act the same way every step: the odd part of a pair, whose
+// The high word of a y with the low-by-low partial product left out: three
+// 32 x 32 -> 64-bit multiply-adds and one add.  a y 2^-64 minus the result
+// lies in [0, 2) (on average about 0.75), so the result is floor(a y 2^-64)
+// or one below it.  The equilibrium's products take this form and add 1 to
+// each result (a bias of about +0.25 instead of -0.75); the adds are folded
+// into per-shell constants where the product feeds a sum.
+__device__ __forceinline__ u64 umulhi_t(u64 a, u64 y) {
+  const unsigned al = (unsigned)a, ah = (unsigned)(a >> 32);
+  const unsigned yl = (unsigned)y, yh = (unsigned)(y >> 32);
+  const u64 lh = (u64)al * yh;
+  const u64 hl = (u64)ah * yl + (lh & 0xFFFFFFFFull);  // < 2^64
+  return (u64)ah * yh + (lh >> 32) + (hl >> 32);
+}
+
+// round(x y 2^-64) (half up) for signed x, unsigned y.  Used where a biased
+// rounding would act the same way every step: the odd part of a pair, whose
 // magnitude a floor after the sign split would always shrink (a momentum
 // damping of 2^-56 per step relative to the odd part).
 __device__ __forceinline__ long long mulhi_su_rn(long long x, u64 y) {
   const u64 lo = (u64)x * y;
   return mulhi_su(x, y) + (long long)(lo >> 63);
+}
+
+// umulhi_t for signed x: x y = (x mod 2^64) y - 2^64 y [x < 0]
+__device__ __forceinline__ u64 mulhi_su_t(long long x, u64 y) {
+  return umulhi_t((u64)x, y) - (y & (u64)(x >> 63));
 }
 
 // floor(x y 2^-sh) for signed x, y and 0 < sh < 64 (the result fits 64 bits)
@@ -392,21 +423,24 @@ __device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParam
   const long long K1 = (rth >> 2) - (rthq >> 3) - (rth2 >> 1);        // Q60
   const u64 K2 = (u64)rth2;                                           // Q64 (rho theta^2 / 8)
   const long long L0 = rB1 - (rth >> 1);                              // Q59
-  const long long L1 = rth;                                           // Q62 (rho theta / 2)
   const long long M0 = rB2 - (rth >> 2) - (rth >> 3);                 // Q59
-  const long long M1 = rth;                                           // Q63 (rho theta / 4)
   const long long mx[3] = {SX, SX + SX, SX + SX + SX};                // Q62
   const long long my[3] = {SY, SY + SY, SY + SY + SY};
+  const u64 kSign = 1ull << 63;
+  const u64 uK0 = (u64)K0, uK1 = (u64)K1 ^ kSign, uL0 = (u64)L0 ^ kSign;  // x + 2^63
+  const u64 uM0 = (u64)M0 ^ kSign, uTH = (u64)rth ^ kSign;                // L1 = M1 = rth
   const double keep = p.one_minus_omega;
-  f[0] = fma(keep, f[0], fx_to_double(mulhi_su(K0, p.fx_c60[0]), p.fx_e[0]));  // x2 = 0
+  f[0] = fma(keep, f[0], fx_to_double((long long)(umulhi_t(uK0, p.fx_c60[0]) - p.fx_d0[0]), p.fx_e[0]));  // x2 = 0
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
-    const long long R0 = mulhi_su(K0, p.fx_c60[k]) + mulhi_su(K1, p.fx_cx2_59[k]) +
-                         (long long)__umul64hi(K2, p.fx_cx4_55[k]);                   // Q55
-    const long long R1 = mulhi_su(L0, p.fx_c62[k]) + mulhi_su(L1, p.fx_cx2_59[k]);    // Q57
-    const long long R2 = mulhi_su(M0, p.fx_c64[k]) + mulhi_su(M1, p.fx_cx2_60[k]);    // Q59
-    const u64 R3 = __umul64hi(R, p.fx_c6[k]);                                         // Q61
-    const u64 R4 = __umul64hi(R, p.fx_c24[k]);                                        // Q63
+    const long long R0 = (long long)(umulhi_t(uK0, p.fx_c60[k]) + umulhi_t(uK1, p.fx_cx2_59[k]) +
+                                     umulhi_t(K2, p.fx_cx4_55[k]) - p.fx_d0[k]);                  // Q55
+    const long long R1 = (long long)(umulhi_t(uL0, p.fx_c62[k]) + umulhi_t(uTH, p.fx_cx2_59[k]) -
+                                     p.fx_d1[k]);                                                 // Q57
+    const long long R2 = (long long)(umulhi_t(uM0, p.fx_c64[k]) + umulhi_t(uTH, p.fx_cx2_60[k]) -
+                                     p.fx_d2[k]);                                                 // Q59
+    const u64 R3 = umulhi_t(R, p.fx_c6[k]);                                                       // Q61
+    const u64 R4 = umulhi_t(R, p.fx_c24[k]);                                                      // Q63
     const int E = p.fx_e[k];
 #pragma unroll
     for (int pr = 0; pr < kPairs; ++pr) {
@@ -414,10 +448,10 @@ __device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParam
       const long long a = fx_hop_dot(pair_cx(pr), pair_cy(pr), mx, my);  // Q62
       const long long sa = a >> 63;                                      // 0 or -1
       const u64 A = (u64)((a ^ sa) - sa);
-      const u64 b = __umul64hi(A, A);                                    // Q60
-      const long long t = R2 + (long long)__umul64hi(b, R4);            // Q59
-      const long long even = R0 + mulhi_su(t, b);                        // Q55
-      const long long s = R1 + (long long)__umul64hi(b, R3);            // Q57
+      const u64 b = umulhi_t(A, A);                                      // Q60
+      const long long t = R2 + (long long)umulhi_t(b, R4);              // Q59 (its +1 in fx_d2)
+      const long long even = R0 + (long long)mulhi_su_t(t, b);          // Q55 (its +1 in fx_d0)
+      const long long s = R1 + (long long)umulhi_t(b, R3);              // Q57 (its +1 in fx_d1)
       const long long oa = mulhi_su_rn(s, A);                            // Q55: |a| (R1 + b R3)
       const long long odd = (oa ^ sa) - sa;                              // the sign of a
       f[1 + 2 * pr] = fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E));

@@ -33,6 +33,29 @@ def mulhi_su(x, y):  # signed x, unsigned y: floor(x y 2^-64)
     return (x * y) >> 64
 
 
+def umulhi_t(a, y):
+    """High word of a y without the low-by-low partial product: three
+    32 x 32 -> 64-bit multiply-adds, the floor or one below it."""
+    assert 0 <= a <= M64 and 0 <= y <= M64
+    al, ah, yl, yh = a & 0xFFFFFFFF, a >> 32, y & 0xFFFFFFFF, y >> 32
+    lh = al * yh
+    hl = ah * yl + (lh & 0xFFFFFFFF)
+    assert hl <= M64
+    r = ah * yh + (lh >> 32) + (hl >> 32)
+    assert (a * y >> 64) - 1 <= r <= a * y >> 64
+    return r
+
+
+def mulhi_su_t(x, y):  # umulhi_t for signed x (mod 2^64, as the kernel's u64)
+    assert -(1 << 63) <= x < (1 << 63) and 0 <= y <= M64
+    return umulhi_t(x & M64, y) - (y if x < 0 else 0)
+
+
+def flip(x):  # x + 2^63 as an unsigned operand: the sign bit flipped
+    assert -(1 << 63) <= x < (1 << 63)
+    return x + (1 << 63)
+
+
 def fits(v, name):
     assert -(1 << 63) <= v < (1 << 63), name
     return v
@@ -53,9 +76,14 @@ def shell_consts(s, c2, w, omega):
     cw = Fr(omega) * Fr(w)
     E = math.frexp(float(cw))[1]
     c = cw / Fr(2) ** E
-    return dict(E=E, c60=round(c * 2**60), c62=round(c * 2**62), c64=round(c * 2**64),
-                cx2_59=round(c * x2 * 2**59), cx2_60=round(c * x2 * 2**60), cx4_55=round(c * x2 * x2 * 2**55),
-                c6=round(c / 6 * 2**64), c24=round(c / 24 * 2**66))
+    C = dict(E=E, c60=round(c * 2**60), c62=round(c * 2**62), c64=round(c * 2**64),
+             cx2_59=round(c * x2 * 2**59), cx2_60=round(c * x2 * 2**60), cx4_55=round(c * x2 * x2 * 2**55),
+             c6=round(c / 6 * 2**64), c24=round(c / 24 * 2**66))
+    # y / 2 of each product with a flipped operand, less the +1 corrections
+    C["d0"] = -1 if c2 == 0 else (C["cx2_59"] >> 1) - 3
+    C["d1"] = (C["c62"] >> 1) + (C["cx2_59"] >> 1) - 3
+    C["d2"] = (C["c64"] >> 1) + (C["cx2_60"] >> 1) - 3
+    return C
 
 
 PAIRS = [(1, 0), (0, 1), (1, 1), (1, -1), (2, 0), (0, 2), (2, 1), (2, -1), (1, 2), (1, -2), (2, 2), (2, -2),
@@ -81,26 +109,28 @@ def equilibrium_fixed(s, shells, wk, R, UX, UY, TH, omega):
     K2 = rth2
     L0 = fits(rB1 - (rth >> 1), "L0")
     M0 = fits(rB2 - (rth >> 2) - (rth >> 3), "M0")
+    assert K0 > 0  # taken as an unsigned operand without the flip
     out = {}
     for k, c2 in enumerate(shells):
         C = shell_consts(s, c2, wk[k], omega)
-        R0 = fits(mulhi_su(K0, C["c60"]) + mulhi_su(K1, C["cx2_59"]) + umulhi(K2, C["cx4_55"]), "R0")
-        R1 = fits(mulhi_su(L0, C["c62"]) + mulhi_su(rth, C["cx2_59"]), "R1")
-        R2 = fits(mulhi_su(M0, C["c64"]) + mulhi_su(rth, C["cx2_60"]), "R2")
-        R3 = fits(umulhi(R, C["c6"]), "R3")
-        R4 = fits(umulhi(R, C["c24"]), "R4")
         if c2 == 0:
-            out[(0, 0)] = Fr(R0) * Fr(2) ** (C["E"] - 55)
+            out[(0, 0)] = Fr(fits(umulhi_t(K0, C["c60"]) - C["d0"], "G0")) * Fr(2) ** (C["E"] - 55)
             continue
+        R0 = fits(umulhi_t(K0, C["c60"]) + umulhi_t(flip(K1), C["cx2_59"]) + umulhi_t(K2, C["cx4_55"]) - C["d0"],
+                  "R0")
+        R1 = fits(umulhi_t(flip(L0), C["c62"]) + umulhi_t(flip(rth), C["cx2_59"]) - C["d1"], "R1")
+        R2 = fits(umulhi_t(flip(M0), C["c64"]) + umulhi_t(flip(rth), C["cx2_60"]) - C["d2"], "R2")
+        R3 = fits(umulhi_t(R, C["c6"]), "R3")
+        R4 = fits(umulhi_t(R, C["c24"]), "R4")
         for cx, cy in PAIRS:
             if cx * cx + cy * cy != c2:
                 continue
             a = fits(cx * SX + cy * SY, "a")
             A = abs(a)
-            b = umulhi(A, A)
-            t = fits(R2 + umulhi(b, R4), "t")
-            even = fits(R0 + mulhi_su(t, b), "even")
-            sv = fits(R1 + umulhi(b, R3), "s")
+            b = umulhi_t(A, A)
+            t = fits(R2 + umulhi_t(b, R4), "t")
+            even = fits(R0 + mulhi_su_t(t, b), "even")
+            sv = fits(R1 + umulhi_t(b, R3), "s")
             oa = (sv * A + (1 << 63)) >> 64  # rounded to nearest
             odd = -oa if a < 0 else oa
             out[(cx, cy)] = Fr(fits(even + odd, "G+")) * Fr(2) ** (C["E"] - 55)
