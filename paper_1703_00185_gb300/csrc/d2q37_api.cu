@@ -62,11 +62,12 @@ void fill_fixed_consts(StepParams& sp) {
     sp.fx_c6[k] = fixed_u64(q6, q6l, 64);
     sp.fx_c24[k] = fixed_u64(q24, q24l, 66);
     // R0 = K0 c60 + (K1 + 2^63) cx2_59 + K2 cx4_55 with the pair's b t product
-    // (four truncated products, three corrections: their mean deficit is about
-    // 0.75 each); R1 = (L0 + 2^63) c62 + (L1 + 2^63) cx2_59 and the pair's b R3;
+    // (four truncated products with a mean deficit of about 0.75 each, and the
+    // +0.5 of the conversion's lowest bit: two corrections);
+    // R1 = (L0 + 2^63) c62 + (L1 + 2^63) cx2_59 and the pair's b R3;
     // R2 = (M0 + 2^63) c64 + (M1 + 2^63) cx2_60 and the pair's b R4 (three
     // products each, three corrections); the shell-0 population is K0 c60 alone
-    sp.fx_d0[k] = k == 0 ? 0ull - 1ull : (sp.fx_cx2_59[k] >> 1) - 3ull;
+    sp.fx_d0[k] = k == 0 ? 0ull - 1ull : (sp.fx_cx2_59[k] >> 1) - 2ull;
     sp.fx_d1[k] = (sp.fx_c62[k] >> 1) + (sp.fx_cx2_59[k] >> 1) - 3ull;
     sp.fx_d2[k] = (sp.fx_c64[k] >> 1) + (sp.fx_cx2_60[k] >> 1) - 3ull;
   }

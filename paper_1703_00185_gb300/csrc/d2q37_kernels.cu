@@ -87,24 +87,32 @@ __device__ __forceinline__ void site_moments_fp64(const double (&f)[kQ], double&
 
 // The same moments with the sums done in 64-bit integers, off the FP64 pipe
 // (GB300 issues 2 FP64 operations per SM per clock but 64+ integer ones).
-// Every population is rounded to the grid of the site's largest exponent,
-// 2^(emax - 1075), i.e. to 53 bits relative to the largest population, and
-// summed exactly: rho and the moment sums carry one rounding per term at
-// that grid (comparable to an FP64 sum) and none from the additions.
+// Every population is rounded down to the grid of the site's largest
+// exponent, 2^(emax - 1075), i.e. to 53 bits relative to the largest
+// population, and summed exactly: rho and the moment sums carry one rounding
+// per term at that grid (comparable to an FP64 sum) and none from the
+// additions.  The roundings are floors, on average 0.5 below for a term whose
+// shift drops many bits and less for the largest populations; the sums of r
+// and e get a constant back (kFloorR, kFloorE: the mean over near-equilibrium
+// states), and those of jx, jy need none (sum c = 0).
 // Headroom: |term| < 2^53, |c|^2 <= 10 and 37 terms keep every sum < 2^62.
 // Sites with a population that is zero-exponent tiny (< 2^-960), infinite or
 // NaN take the FP64 form.
+constexpr long long kFloorR = 18, kFloorE = 107;
+
 __device__ __forceinline__ long long fixed_term(double v, int emax) {
   const int hi = __double2hiint(v);
   const unsigned lo = (unsigned)__double2loint(v);
   const int e = (hi >> 20) & 0x7FF;
   // the implicit one is set for zero and subnormal inputs too: with emax >= 64
-  // their shift is the full 62 and they round to 0, as they should
+  // their shift is the full 62 and they round to 0 (-1 for a negative zero)
   const long long mant = ((long long)((hi & 0xFFFFF) | 0x100000) << 32) | lo;
   const int sh = min(emax - e, 62);
-  const long long r = (((mant << 1) >> sh) + 1) >> 1;  // mant 2^-sh rounded half up
-  const long long s = hi >> 31;                       // 0 or -1
-  return (r ^ s) - s;
+  const long long s = hi >> 31;  // 0 or -1
+  // a negative v as the one's complement of its magnitude, -mant - 1: its
+  // arithmetic shift is floor(v 2^-sh) or, when the dropped bits are all zero,
+  // one below it
+  return (mant ^ s) >> sh;
 }
 
 // The exact sums r = sum f, jx, jy = sum c f, e = sum |c|^2 f on the grid
@@ -130,8 +138,8 @@ __device__ __forceinline__ bool site_sums(const double (&f)[kQ], long long& r, l
     jx += pair_cx(p) * d;
     jy += pair_cy(p) * d;
   }
-  r = sh[0];
-  e = 0;
+  r = sh[0] + kFloorR;
+  e = kFloorE;
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
     r += sh[k];
@@ -203,8 +211,9 @@ __device__ __forceinline__ double hop_dot(int cx, int cy, const double (&mx)[3],
 // bit flipped): x y 2^-64 = (x + 2^63) y 2^-64 - y / 2, and the y / 2 terms
 // and the corrections of a shell are one constant subtracted from R0, R1 and
 // R2 (fx_d0, fx_d1, fx_d2).  K0 > 0.74 rho inside the ranges and needs no
-// shift.  The corrections make the equilibrium's mass bias +1.4e-17 per
-// collision relative to omega rho (the floors of exact products: -7.6e-17).
+// shift.  With the set lowest bit of the conversion (+0.5 on average), the
+// corrections make the equilibrium's mass bias +0.2e-17 per collision
+// relative to omega rho (the floors of exact products: -7.6e-17).
 // The odd part keeps an exact, rounded product: a bias there acts on the
 // momentum the same way every step.
 constexpr int kFxOut = 55;  // format of R0 and of the results G = even +- odd
@@ -281,10 +290,11 @@ __device__ __forceinline__ long long to_fx(double v) {
 #endif
 
 #if D2Q37_FX_CVT != 0
+// g != 0
 __device__ __forceinline__ double fx_to_double_fp64(long long g, int E) {
   const double d = (double)g;  // exact up to its one rounding
   const u64 bits = (u64)__double_as_longlong(d) + ((u64)(long long)(E - kFxOut) << 52);
-  return g ? __longlong_as_double((long long)bits) : 0.0;
+  return __longlong_as_double((long long)bits);
 }
 #endif
 
@@ -316,11 +326,14 @@ __device__ __forceinline__ double fx_to_double_int(long long g, int E) {
 }
 #endif
 
+// The lowest bit of g is set first: g is never zero (which the exponent add
+// of the FP64 form needs), and it is 0.5 larger on average, which the
+// per-shell corrections of the equilibrium take into account.
 __device__ __forceinline__ double fx_to_double(long long g, int E) {
 #if D2Q37_FX_CVT == 0
-  return fx_to_double_int(g, E);
+  return fx_to_double_int(g | 1, E);
 #else
-  return fx_to_double_fp64(g, E);
+  return fx_to_double_fp64(g | 1, E);
 #endif
 }
 

@@ -80,7 +80,7 @@ def shell_consts(s, c2, w, omega):
              cx2_59=round(c * x2 * 2**59), cx2_60=round(c * x2 * 2**60), cx4_55=round(c * x2 * x2 * 2**55),
              c6=round(c / 6 * 2**64), c24=round(c / 24 * 2**66))
     # y / 2 of each product with a flipped operand, less the +1 corrections
-    C["d0"] = -1 if c2 == 0 else (C["cx2_59"] >> 1) - 3
+    C["d0"] = -1 if c2 == 0 else (C["cx2_59"] >> 1) - 2
     C["d1"] = (C["c62"] >> 1) + (C["cx2_59"] >> 1) - 3
     C["d2"] = (C["c64"] >> 1) + (C["cx2_60"] >> 1) - 3
     return C
@@ -114,7 +114,7 @@ def equilibrium_fixed(s, shells, wk, R, UX, UY, TH, omega):
     for k, c2 in enumerate(shells):
         C = shell_consts(s, c2, wk[k], omega)
         if c2 == 0:
-            out[(0, 0)] = Fr(fits(umulhi_t(K0, C["c60"]) - C["d0"], "G0")) * Fr(2) ** (C["E"] - 55)
+            out[(0, 0)] = Fr(fits(umulhi_t(K0, C["c60"]) - C["d0"], "G0") | 1) * Fr(2) ** (C["E"] - 55)
             continue
         R0 = fits(umulhi_t(K0, C["c60"]) + umulhi_t(flip(K1), C["cx2_59"]) + umulhi_t(K2, C["cx4_55"]) - C["d0"],
                   "R0")
@@ -133,8 +133,9 @@ def equilibrium_fixed(s, shells, wk, R, UX, UY, TH, omega):
             sv = fits(R1 + umulhi_t(b, R3), "s")
             oa = (sv * A + (1 << 63)) >> 64  # rounded to nearest
             odd = -oa if a < 0 else oa
-            out[(cx, cy)] = Fr(fits(even + odd, "G+")) * Fr(2) ** (C["E"] - 55)
-            out[(-cx, -cy)] = Fr(fits(even - odd, "G-")) * Fr(2) ** (C["E"] - 55)
+            # the conversion sets the lowest bit (never zero)
+            out[(cx, cy)] = Fr(fits(even + odd, "G+") | 1) * Fr(2) ** (C["E"] - 55)
+            out[(-cx, -cy)] = Fr(fits(even - odd, "G-") | 1) * Fr(2) ** (C["E"] - 55)
     return out
 
 
