@@ -203,18 +203,16 @@ __device__ __forceinline__ double hop_dot(int cx, int cy, const double (&mx)[3],
 //   R0 = c (K0 + x2 K1 + x2^2 K2),  R1 = c (L0 + x2 L1),  R2 = c (M0 + x2 M1),
 //   R3 = c rho / 6,  R4 = c rho / 24,
 // and per pair even = R0 + b (R2 + b R4), odd = a (R1 + b R3), b = a^2.
-// The site values' products are exact high words (floor).  The per-shell
-// products (9 per shell) and the even part's per-pair products (b, t, the
-// even product, and the one of s) are umulhi_t, three multiply-adds instead
-// of four, with integer corrections folded into per-shell constants.  A
-// signed site value x meets the unsigned shell constants as x + 2^63 (its sign
-// bit flipped): x y 2^-64 = (x + 2^63) y 2^-64 - y / 2, and the y / 2 terms
-// and the corrections of a shell are one constant subtracted from R0, R1 and
-// R2 (fx_d0, fx_d1, fx_d2).  K0 > 0.74 rho inside the ranges and needs no
-// shift.  With the set lowest bit of the conversion (+0.5 on average), the
-// corrections make the equilibrium's mass bias +0.2e-17 per collision
-// relative to omega rho (the floors of exact products: -7.6e-17).
-// The odd part keeps an exact, rounded product: a bias there acts on the
+// A signed site value x meets the unsigned shell constants as x + 2^63 (its
+// sign bit flipped), which needs no sign fix: x y 2^-64 = (x + 2^63) y 2^-64
+// - y / 2, and the y / 2 terms of a shell are one constant subtracted from R0,
+// R1 and R2 (fx_d0, fx_d1, fx_d2), together with a correction of +1 for the
+// roundings of its sums and per-pair products (0.5 below on average for an
+// exact high word, 0.75 for umulhi_t).  K0 > 0.74 rho inside the ranges and
+// needs no shift.  With the set lowest bit of the conversion (+0.5 on
+// average), the equilibrium's mass bias is -1.6e-17 per collision relative
+// to omega rho (without the corrections: -7.6e-17).
+// The odd part takes a rounded product: a bias there would act on the
 // momentum the same way every step.
 constexpr int kFxOut = 55;  // format of R0 and of the results G = even +- odd
 
@@ -226,17 +224,21 @@ __device__ __forceinline__ long long mulhi_su(long long x, u64 y) {
 }
 
 // The high word of a y with the low-by-low partial product left out: three
-// 32 x 32 -> 64-bit multiply-adds and one add.  a y 2^-64 minus the result
-// lies in [0, 2) (on average about 0.75), so the result is floor(a y 2^-64)
-// or one below it.  The equilibrium's products take this form and add 1 to
-// each result (a bias of about +0.25 instead of -0.75); the adds are folded
-// into per-shell constants where the product feeds a sum.
+// 32 x 32 -> 64-bit multiply-adds and one add, the floor of a y 2^-64 or one
+// below it (0.75 below a y 2^-64 on average).  More instructions than the
+// exact high word but a shorter dependency chain: the per-pair products,
+// which form one chain per pair, take this form.
 __device__ __forceinline__ u64 umulhi_t(u64 a, u64 y) {
   const unsigned al = (unsigned)a, ah = (unsigned)(a >> 32);
   const unsigned yl = (unsigned)y, yh = (unsigned)(y >> 32);
   const u64 lh = (u64)al * yh;
   const u64 hl = (u64)ah * yl + (lh & 0xFFFFFFFFull);  // < 2^64
   return (u64)ah * yh + (lh >> 32) + (hl >> 32);
+}
+
+// umulhi_t for signed x: x y = (x mod 2^64) y - 2^64 y [x < 0]
+__device__ __forceinline__ long long mulhi_su_t(long long x, u64 y) {
+  return (long long)(umulhi_t((u64)x, y) - (y & (u64)(x >> 63)));
 }
 
 // round(x y 2^-64) (half up) for signed x, unsigned y.  Used where a biased
@@ -246,11 +248,6 @@ __device__ __forceinline__ u64 umulhi_t(u64 a, u64 y) {
 __device__ __forceinline__ long long mulhi_su_rn(long long x, u64 y) {
   const u64 lo = (u64)x * y;
   return mulhi_su(x, y) + (long long)(lo >> 63);
-}
-
-// umulhi_t for signed x: x y = (x mod 2^64) y - 2^64 y [x < 0]
-__device__ __forceinline__ u64 mulhi_su_t(long long x, u64 y) {
-  return umulhi_t((u64)x, y) - (y & (u64)(x >> 63));
 }
 
 // floor(x y 2^-sh) for signed x, y and 0 < sh < 64 (the result fits 64 bits)
@@ -443,17 +440,17 @@ __device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParam
   const u64 uK0 = (u64)K0, uK1 = (u64)K1 ^ kSign, uL0 = (u64)L0 ^ kSign;  // x + 2^63
   const u64 uM0 = (u64)M0 ^ kSign, uTH = (u64)rth ^ kSign;                // L1 = M1 = rth
   const double keep = p.one_minus_omega;
-  f[0] = fma(keep, f[0], fx_to_double((long long)(umulhi_t(uK0, p.fx_c60[0]) - p.fx_d0[0]), p.fx_e[0]));  // x2 = 0
+  f[0] = fma(keep, f[0], fx_to_double((long long)(__umul64hi(uK0, p.fx_c60[0]) - p.fx_d0[0]), p.fx_e[0]));  // x2 = 0
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
-    const long long R0 = (long long)(umulhi_t(uK0, p.fx_c60[k]) + umulhi_t(uK1, p.fx_cx2_59[k]) +
-                                     umulhi_t(K2, p.fx_cx4_55[k]) - p.fx_d0[k]);                  // Q55
-    const long long R1 = (long long)(umulhi_t(uL0, p.fx_c62[k]) + umulhi_t(uTH, p.fx_cx2_59[k]) -
-                                     p.fx_d1[k]);                                                 // Q57
-    const long long R2 = (long long)(umulhi_t(uM0, p.fx_c64[k]) + umulhi_t(uTH, p.fx_cx2_60[k]) -
-                                     p.fx_d2[k]);                                                 // Q59
-    const u64 R3 = umulhi_t(R, p.fx_c6[k]);                                                       // Q61
-    const u64 R4 = umulhi_t(R, p.fx_c24[k]);                                                      // Q63
+    const long long R0 = (long long)(__umul64hi(uK0, p.fx_c60[k]) + __umul64hi(uK1, p.fx_cx2_59[k]) +
+                                     __umul64hi(K2, p.fx_cx4_55[k]) - p.fx_d0[k]);  // Q55
+    const long long R1 = (long long)(__umul64hi(uL0, p.fx_c62[k]) + __umul64hi(uTH, p.fx_cx2_59[k]) -
+                                     p.fx_d1[k]);  // Q57
+    const long long R2 = (long long)(__umul64hi(uM0, p.fx_c64[k]) + __umul64hi(uTH, p.fx_cx2_60[k]) -
+                                     p.fx_d2[k]);  // Q59
+    const u64 R3 = __umul64hi(R, p.fx_c6[k]);   // Q61
+    const u64 R4 = __umul64hi(R, p.fx_c24[k]);  // Q63
     const int E = p.fx_e[k];
 #pragma unroll
     for (int pr = 0; pr < kPairs; ++pr) {
@@ -462,9 +459,9 @@ __device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParam
       const long long sa = a >> 63;                                      // 0 or -1
       const u64 A = (u64)((a ^ sa) - sa);
       const u64 b = umulhi_t(A, A);                                      // Q60
-      const long long t = R2 + (long long)umulhi_t(b, R4);              // Q59 (its +1 in fx_d2)
-      const long long even = R0 + (long long)mulhi_su_t(t, b);          // Q55 (its +1 in fx_d0)
-      const long long s = R1 + (long long)umulhi_t(b, R3);              // Q57 (its +1 in fx_d1)
+      const long long t = R2 + (long long)umulhi_t(b, R4);              // Q59
+      const long long even = R0 + mulhi_su_t(t, b);                      // Q55
+      const long long s = R1 + (long long)umulhi_t(b, R3);              // Q57
       const long long oa = mulhi_su_rn(s, A);                            // Q55: |a| (R1 + b R3)
       const long long odd = (oa ^ sa) - sa;                              // the sign of a
       f[1 + 2 * pr] = fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E));

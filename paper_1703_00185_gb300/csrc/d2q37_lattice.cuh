@@ -145,8 +145,8 @@ struct StepParams {
   unsigned long long fx_cx2_59[kShells], fx_cx2_60[kShells], fx_cx4_55[kShells];
   unsigned long long fx_c6[kShells], fx_c24[kShells];
   // subtracted from R0, R1, R2 (mod 2^64): y / 2 for each product whose site
-  // value enters with its sign bit flipped (x + 2^63), less the corrections of
-  // the truncated products the sum and its per-pair product carry
+  // value enters with its sign bit flipped (x + 2^63), less a rounding
+  // correction
   unsigned long long fx_d0[kShells], fx_d1[kShells], fx_d2[kShells];
   int fx_e[kShells];
   unsigned long long fx_s62;  // s 2^62

@@ -79,10 +79,10 @@ def shell_consts(s, c2, w, omega):
     C = dict(E=E, c60=round(c * 2**60), c62=round(c * 2**62), c64=round(c * 2**64),
              cx2_59=round(c * x2 * 2**59), cx2_60=round(c * x2 * 2**60), cx4_55=round(c * x2 * x2 * 2**55),
              c6=round(c / 6 * 2**64), c24=round(c / 24 * 2**66))
-    # y / 2 of each product with a flipped operand, less the +1 corrections
-    C["d0"] = -1 if c2 == 0 else (C["cx2_59"] >> 1) - 2
-    C["d1"] = (C["c62"] >> 1) + (C["cx2_59"] >> 1) - 3
-    C["d2"] = (C["c64"] >> 1) + (C["cx2_60"] >> 1) - 3
+    # y / 2 of each product with a flipped operand, less a rounding correction
+    C["d0"] = 0 if c2 == 0 else (C["cx2_59"] >> 1) - 1
+    C["d1"] = (C["c62"] >> 1) + (C["cx2_59"] >> 1) - 1
+    C["d2"] = (C["c64"] >> 1) + (C["cx2_60"] >> 1) - 1
     return C
 
 
@@ -114,14 +114,14 @@ def equilibrium_fixed(s, shells, wk, R, UX, UY, TH, omega):
     for k, c2 in enumerate(shells):
         C = shell_consts(s, c2, wk[k], omega)
         if c2 == 0:
-            out[(0, 0)] = Fr(fits(umulhi_t(K0, C["c60"]) - C["d0"], "G0") | 1) * Fr(2) ** (C["E"] - 55)
+            out[(0, 0)] = Fr(fits(umulhi(K0, C["c60"]) - C["d0"], "G0") | 1) * Fr(2) ** (C["E"] - 55)
             continue
-        R0 = fits(umulhi_t(K0, C["c60"]) + umulhi_t(flip(K1), C["cx2_59"]) + umulhi_t(K2, C["cx4_55"]) - C["d0"],
+        R0 = fits(umulhi(K0, C["c60"]) + umulhi(flip(K1), C["cx2_59"]) + umulhi(K2, C["cx4_55"]) - C["d0"],
                   "R0")
-        R1 = fits(umulhi_t(flip(L0), C["c62"]) + umulhi_t(flip(rth), C["cx2_59"]) - C["d1"], "R1")
-        R2 = fits(umulhi_t(flip(M0), C["c64"]) + umulhi_t(flip(rth), C["cx2_60"]) - C["d2"], "R2")
-        R3 = fits(umulhi_t(R, C["c6"]), "R3")
-        R4 = fits(umulhi_t(R, C["c24"]), "R4")
+        R1 = fits(umulhi(flip(L0), C["c62"]) + umulhi(flip(rth), C["cx2_59"]) - C["d1"], "R1")
+        R2 = fits(umulhi(flip(M0), C["c64"]) + umulhi(flip(rth), C["cx2_60"]) - C["d2"], "R2")
+        R3 = fits(umulhi(R, C["c6"]), "R3")
+        R4 = fits(umulhi(R, C["c24"]), "R4")
         for cx, cy in PAIRS:
             if cx * cx + cy * cy != c2:
                 continue
