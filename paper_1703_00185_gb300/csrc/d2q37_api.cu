@@ -171,6 +171,10 @@ void fill_step_params(lbm_t* h) {
   sp.Hy = halo_rows(h->prec);
   sp.periodic_y = h->prm.periodic_y ? 1 : 0;
   sp.plane = (long long)h->NX * h->NY;
+  for (int l = 0; l < kQ; ++l) {
+    sp.pull_off[l] = (l * sp.plane - kCx[l] * (long long)sp.NY - kCy[l]) * (long long)sizeof(double);
+    sp.plane_off[l] = l * sp.plane * (long long)sizeof(double);
+  }
   const double tau = h->prm.tau;
   sp.omega = 1.0 / tau;
   sp.one_minus_omega = 1.0 - sp.omega;

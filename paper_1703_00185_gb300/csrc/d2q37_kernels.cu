@@ -560,12 +560,21 @@ __device__ __forceinline__ double wall_density(const double* __restrict__ src, c
 // (the pbc step folded into the writer; the halo columns see the same values
 // the wrap kernel would copy).  x is uniform across a block, so the extra
 // stores are divergence-free except on periodic y edges.
+// OFF: address the planes with the byte offsets of p (read from the constant
+// bank by the single-lattice kernels) instead of multiples of p.plane.
+template <bool OFF = false>
 __device__ __forceinline__ void store_site(double* __restrict__ dst, const StepParams& p, int x, int y,
                                            const double (&f)[kQ]) {
   if (x >= kHx && x < p.Lx - kHx && (!p.periodic_y || (y >= kHx && y < p.Ly - kHx))) {
     const long long i = site_index(p, x, y);  // no halo image: the common case
+    if constexpr (OFF) {
+      char* d = (char*)(dst + i);
 #pragma unroll
-    for (int l = 0; l < kQ; ++l) dst[l * p.plane + i] = f[l];
+      for (int l = 0; l < kQ; ++l) *(double*)(d + p.plane_off[l]) = f[l];
+    } else {
+#pragma unroll
+      for (int l = 0; l < kQ; ++l) dst[l * p.plane + i] = f[l];
+    }
     return;
   }
   int xs[3] = {x, 0, 0}, ys[3] = {y, 0, 0};
@@ -646,25 +655,32 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) collide_kernel
   const int x = blockIdx.x;
   const int y = blockIdx.y * kBlockY + threadIdx.x;
   if (y >= p.Ly) return;
-  const long long i = site_index(p, x, y);
+  const char* s = (const char*)(buf + site_index(p, x, y));
   double f[kQ];
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) f[l] = buf[l * p.plane + i];
+  for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(s + p.plane_off[l]);
   collide_site(f, p);
-  store_site(buf, p, x, y, f);
+  store_site<true>(buf, p, x, y, f);
 }
 
 // One site of the fused step: gather (pull), wall bc on the wall bands,
 // collide, store with halo images.
 // p: the lattice (geometry, walls); px: the constants of its collision (tau,
 // g: the fixed-point tables, omega, the field shifts), the same object for a
-// single lattice.
+// single lattice.  OFF: addresses from the byte offsets of p (see store_site).
+template <bool OFF>
 __device__ __forceinline__ void fused_site(const double* __restrict__ src, double* __restrict__ dst,
                                            const StepParams& p, const StepParams& px, int x, int y) {
   const long long i = site_index(p, x, y);
   double f[kQ];
+  if constexpr (OFF) {
+    const char* s = (const char*)(src + i);
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) f[l] = src[l * p.plane + i - vel_cx(l) * p.NY - vel_cy(l)];
+    for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(s + p.pull_off[l]);
+  } else {
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) f[l] = src[l * p.plane + i - vel_cx(l) * p.NY - vel_cy(l)];
+  }
   if (!p.periodic_y && (y < 3 || y >= p.Ly - 3)) {
     const int wall = y >= p.Ly - 3;
     const int r = wall ? p.Ly - 1 - y : y;
@@ -676,7 +692,7 @@ __device__ __forceinline__ void fused_site(const double* __restrict__ src, doubl
     }
   }
   collide_site(f, px);
-  store_site(dst, p, x, y, f);
+  store_site<OFF>(dst, p, x, y, f);
 }
 
 __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(const double* __restrict__ src, double* __restrict__ dst,
@@ -684,7 +700,7 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(c
   const int x = blockIdx.x;
   const int y = blockIdx.y * kBlockY + threadIdx.x;
   if (y >= p.Ly) return;
-  fused_site(src, dst, p, p, x, y);
+  fused_site<true>(src, dst, p, p, x, y);
 }
 
 // Many lattices in one launch: block-sized tiles (one column x, BY
@@ -707,7 +723,7 @@ __global__ void __launch_bounds__(BY, (D2Q37_BATCH_MIN_BLOCKS * 128) / BY > 0 ? 
     const int y = (local - x * e.ytiles) * BY + threadIdx.x;
     const int c = e.cur ^ parity;
     if (y < e.p.Ly)
-      fused_site((const double*)e.buf[c], (double*)e.buf[c ^ 1], e.p, UNIFORM ? common : e.p, x, y);
+      fused_site<false>((const double*)e.buf[c], (double*)e.buf[c ^ 1], e.p, UNIFORM ? common : e.p, x, y);
   }
 }
 

@@ -122,6 +122,9 @@ struct StepParams {
   int Hy;          // halo rows below the lattice (16 for FP64, 32 for FP32 storage)
   int periodic_y;
   long long plane; // population plane stride (elements) = (Lx + 2 kHx) * NY
+  // byte offsets from a site to the source of its pull (l plane - c_l . (NY, 1))
+  // and to its population planes (l plane), for the single-lattice kernels
+  long long pull_off[kQ], plane_off[kQ];
   float omega_f, keep_f;  // 1/tau and 1 - 1/tau rounded to FP32 (FP32 storage)
   float uy_shift_df[2];    // uy_shift and theta_shift as double-float (hi, lo) pairs
   float theta_shift_df[2];
