@@ -62,11 +62,11 @@ void fill_fixed_consts(StepParams& sp) {
     sp.fx_c6[k] = fixed_u64(q6, q6l, 64);
     sp.fx_c24[k] = fixed_u64(q24, q24l, 66);
     // R0 = K0 c60 + (K1 + 2^63) cx2_59 + K2 cx4_55, R1 = (L0 + 2^63) c62 +
-    // (L1 + 2^63) cx2_59, R2 = (M0 + 2^63) c64 + (M1 + 2^63) cx2_60, each with
-    // a correction of +1 for its floors and those of the pair's product it
-    // feeds (b t, b R3, b R4; with the conversion's lowest bit for R0); the
-    // shell-0 population, K0 c60 alone, needs none
-    sp.fx_d0[k] = k == 0 ? 0ull : (sp.fx_cx2_59[k] >> 1) - 1ull;
+    // (L1 + 2^63) cx2_59, R2 = (M0 + 2^63) c64 + (M1 + 2^63) cx2_60, with
+    // corrections for their floors and those of the pair's product each
+    // feeds (b t, b R3, b R4; with the conversion's lowest bit for R0): +2 for
+    // R0, +1 for R1 and R2; the shell-0 population, K0 c60 alone, needs none
+    sp.fx_d0[k] = k == 0 ? 0ull : (sp.fx_cx2_59[k] >> 1) - 2ull;
     sp.fx_d1[k] = (sp.fx_c62[k] >> 1) + (sp.fx_cx2_59[k] >> 1) - 1ull;
     sp.fx_d2[k] = (sp.fx_c64[k] >> 1) + (sp.fx_cx2_60[k] >> 1) - 1ull;
   }

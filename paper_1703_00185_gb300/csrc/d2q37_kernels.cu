@@ -93,12 +93,14 @@ __device__ __forceinline__ void site_moments_fp64(const double (&f)[kQ], double&
 // per term at that grid (comparable to an FP64 sum) and none from the
 // additions.  The roundings are floors, on average 0.5 below for a term whose
 // shift drops many bits and less for the largest populations; the sums of r
-// and e get a constant back (kFloorR, kFloorE: the mean over near-equilibrium
-// states), and those of jx, jy need none (sum c = 0).
+// and e get a constant back (kFloorR, kFloorE: the mean deficits over
+// near-equilibrium states, 16.3 and 104.8 grid units), and those of jx, jy
+// need none (sum c = 0).  The remaining -0.3 units of r (-1.2e-17 of rho)
+// offset most of the equilibrium's +1.7e-17 (see fx_d0).
 // Headroom: |term| < 2^53, |c|^2 <= 10 and 37 terms keep every sum < 2^62.
 // Sites with a population that is zero-exponent tiny (< 2^-960), infinite or
 // NaN take the FP64 form.
-constexpr long long kFloorR = 18, kFloorE = 107;
+constexpr long long kFloorR = 16, kFloorE = 105;
 
 __device__ __forceinline__ long long fixed_term(double v, int emax) {
   const int hi = __double2hiint(v);
@@ -206,12 +208,13 @@ __device__ __forceinline__ double hop_dot(int cx, int cy, const double (&mx)[3],
 // A signed site value x meets the unsigned shell constants as x + 2^63 (its
 // sign bit flipped), which needs no sign fix: x y 2^-64 = (x + 2^63) y 2^-64
 // - y / 2, and the y / 2 terms of a shell are one constant subtracted from R0,
-// R1 and R2 (fx_d0, fx_d1, fx_d2), together with a correction of +1 for the
+// R1 and R2 (fx_d0, fx_d1, fx_d2), together with corrections for the
 // roundings of its sums and per-pair products (0.5 below on average for an
 // exact high word, 0.75 for umulhi_t).  K0 > 0.74 rho inside the ranges and
 // needs no shift.  With the set lowest bit of the conversion (+0.5 on
-// average), the equilibrium's mass bias is -1.6e-17 per collision relative
-// to omega rho (without the corrections: -7.6e-17).
+// average) and two corrections in fx_d0, the equilibrium's mass bias is
+// +1.7e-17 per collision relative to omega rho (without the corrections:
+// -7.6e-17), which the moment sums' -1.2e-17 nearly cancels.
 // The odd part takes a rounded product: a bias there would act on the
 // momentum the same way every step.
 constexpr int kFxOut = 55;  // format of R0 and of the results G = even +- odd

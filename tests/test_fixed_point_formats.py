@@ -11,7 +11,9 @@ are better than FP64 rounding.  It is a check of the formats, not of the
 kernel: the kernel itself is held to the oracle by the GPU tests.
 """
 import math
+import os
 import random
+import re
 import struct
 from fractions import Fraction as Fr
 
@@ -80,7 +82,7 @@ def shell_consts(s, c2, w, omega):
              cx2_59=round(c * x2 * 2**59), cx2_60=round(c * x2 * 2**60), cx4_55=round(c * x2 * x2 * 2**55),
              c6=round(c / 6 * 2**64), c24=round(c / 24 * 2**66))
     # y / 2 of each product with a flipped operand, less a rounding correction
-    C["d0"] = 0 if c2 == 0 else (C["cx2_59"] >> 1) - 1
+    C["d0"] = 0 if c2 == 0 else (C["cx2_59"] >> 1) - 2
     C["d1"] = (C["c62"] >> 1) + (C["cx2_59"] >> 1) - 1
     C["d2"] = (C["c64"] >> 1) + (C["cx2_60"] >> 1) - 1
     return C
@@ -252,3 +254,53 @@ def test_site_values_from_sums(quad):
         assert abs(Fr(UY, 2**64) - UYe) < Fr(1, 10**17)
         assert abs(Fr(TH, 2**62) - THe) < Fr(1, 10**17)
     assert inside > 100
+
+
+# The FP64 step's exact moment sums round every population down to the grid
+# 2^(emax - 1075) of the site's largest exponent (a negative one through the
+# one's complement of its magnitude) and give the mean deficit back as
+# constants: kFloorR to r = sum f, kFloorE to e = sum |c|^2 f (jx, jy need
+# none: sum c = 0).  The kernel's constants, read from its source:
+_KSRC = open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "paper_1703_00185_gb300", "csrc",
+                          "d2q37_kernels.cu")).read()
+FLOOR_R, FLOOR_E = (int(v) for v in re.search(r"kFloorR = (\d+), kFloorE = (\d+);", _KSRC).groups())
+
+
+def floor_deficits(f, c2):
+    """Per site (rows of f), the deficits sum_l (exact - floored) and
+    sum_l |c_l|^2 (exact - floored) of the kernel's conversion, in grid units."""
+    bits = f.view(np.int64)
+    hi = bits >> 32
+    e = (hi >> 20) & 0x7FF
+    emax = ((hi & 0x7FFFFFFF) >> 20).max(axis=1, keepdims=True)
+    mant = (bits & ((1 << 52) - 1)) | (1 << 52)
+    sh = np.minimum(emax - e, 62)
+    neg = hi < 0
+    got = np.where(neg, ~mant, mant) >> sh  # the kernel's term
+    # exact value on the grid: +-mant 2^-sh; the deficit is computed in two
+    # integer parts so that no float rounding enters
+    whole = np.where(neg, -((mant + (1 << sh) - 1) >> sh), mant >> sh)
+    rem = np.where(neg, (-mant) & ((1 << sh) - 1), mant & ((1 << sh) - 1))
+    deficit = (whole - got) + rem / np.exp2(sh.astype(float))
+    return deficit.sum(axis=1), (deficit * np.asarray(c2)).sum(axis=1)
+
+
+def test_moment_floor_compensation():
+    """The constants are the mean deficits (to the nearest integer) over
+    near-equilibrium sites: the oracle's equilibria over the step's range of
+    states (including the cold ones with negative populations), perturbed by
+    1 %.  Every single deficit stays within [0, 37] (r) and [0, 216] (e)."""
+    cx, cy = oracle.velocity_set()
+    c2 = (np.asarray(cx) ** 2 + np.asarray(cy) ** 2)
+    rng = np.random.default_rng(17)
+    n = 4000
+    rho = rng.uniform(0.7, 1.4, n)
+    ux, uy = rng.uniform(-0.1, 0.1, n), rng.uniform(-0.1, 0.1, n)
+    T = rng.uniform(0.5, 1.5, n)
+    f = np.stack([oracle.equilibrium(rho[i], ux[i], uy[i], T[i]) for i in range(n)])
+    f = f * (1.0 + 0.01 * rng.standard_normal(f.shape))
+    assert (f < 0).any(axis=1).mean() > 0.1  # cold sites with negative populations are in the sample
+    dr, de = floor_deficits(np.ascontiguousarray(f), c2)
+    assert dr.min() >= 0 and dr.max() <= 37 and de.min() >= 0 and de.max() <= c2.sum()
+    assert abs(dr.mean() - FLOOR_R) <= 0.5, dr.mean()
+    assert abs(de.mean() - FLOOR_E) <= 0.5, de.mean()
