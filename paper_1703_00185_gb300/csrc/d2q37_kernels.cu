@@ -248,9 +248,15 @@ __device__ __forceinline__ long long mulhi_su_t(long long x, u64 y) {
 // rounding would act the same way every step: the odd part of a pair, whose
 // magnitude a floor after the sign split would always shrink (a momentum
 // damping of 2^-56 per step relative to the odd part).
+// The four 32 x 32-bit partial products are independent; the rounding half
+// (2^63 of the 128-bit product) enters the middle column as 2^31.
 __device__ __forceinline__ long long mulhi_su_rn(long long x, u64 y) {
-  const u64 lo = (u64)x * y;
-  return mulhi_su(x, y) + (long long)(lo >> 63);
+  const unsigned xl = (unsigned)x, xh = (unsigned)((u64)x >> 32);
+  const unsigned yl = (unsigned)y, yh = (unsigned)(y >> 32);
+  const u64 ll = (u64)xl * yl, lh = (u64)xl * yh, hl = (u64)xh * yl, hh = (u64)xh * yh;
+  const u64 mid = (ll >> 32) + (lh & 0xFFFFFFFFull) + (hl & 0xFFFFFFFFull) + 0x80000000ull;  // < 2^34
+  const u64 hi = hh + (lh >> 32) + (hl >> 32) + (mid >> 32);  // floor(((x mod 2^64) y + 2^63) 2^-64)
+  return (long long)(hi - (y & (u64)(x >> 63)));
 }
 
 // floor(x y 2^-sh) for signed x, y and 0 < sh < 64 (the result fits 64 bits)
