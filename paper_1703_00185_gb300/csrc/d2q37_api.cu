@@ -58,9 +58,7 @@ void fill_fixed_consts(StepParams& sp) {
     sp.fx_cx2_60[k] = fixed_u64(p1h, p1l, 60);
     sp.fx_cx4_55[k] = fixed_u64(p2h, p2l, 55);
     const double q6 = ch / 6.0, q6l = (std::fma(-q6, 6.0, ch) + cl) / 6.0;
-    const double q24 = ch / 24.0, q24l = (std::fma(-q24, 24.0, ch) + cl) / 24.0;
-    sp.fx_c6[k] = fixed_u64(q6, q6l, 64);
-    sp.fx_c24[k] = fixed_u64(q24, q24l, 66);
+    sp.fx_c6[k] = fixed_u64(q6, q6l, 64);  // also (c/24) 2^66: one product serves R3 and R4
     // R0 = K0 c60 + (K1 + 2^63) cx2_59 + K2 cx4_55, R1 = (L0 + 2^63) c62 +
     // (L1 + 2^63) cx2_59, R2 = (M0 + 2^63) c64 + (M1 + 2^63) cx2_60, with
     // corrections for their floors and those of the pair's product each

@@ -419,9 +419,24 @@ __device__ __forceinline__ bool fx_site_from_sums(long long r, long long jx, lon
   return true;
 }
 
+// Where a collision puts the relaxed populations: back into the site's
+// register array, or straight into the site's planes of the destination, so
+// that each pair's registers are free once it is relaxed.
+struct InPlace {
+  double (&f)[kQ];
+  __device__ __forceinline__ void put(int l, double v) const { f[l] = v; }
+};
+struct ToPlanes {
+  char* d;              // the site's element of plane 0
+  const StepParams& p;  // plane_off
+  __device__ __forceinline__ void put(int l, double v) const { *(double*)(d + p.plane_off[l]) = v; }
+};
+
 // The collision of collide_site_fp64 below with the equilibrium in fixed
 // point (formats in the comments), for a site inside the fixed-point ranges.
-__device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParams& p, const FxSite& fs) {
+template <class O>
+__device__ __forceinline__ void collide_site_fx(const double (&f)[kQ], const StepParams& p, const FxSite& fs,
+                                                const O& out) {
   const long long UX = fs.UX, UY = fs.UY;  // Q64
   const long long TH = fs.TH;              // Q62
   const u64 R = fs.R;                      // Q61
@@ -449,7 +464,7 @@ __device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParam
   const u64 uK0 = (u64)K0, uK1 = (u64)K1 ^ kSign, uL0 = (u64)L0 ^ kSign;  // x + 2^63
   const u64 uM0 = (u64)M0 ^ kSign, uTH = (u64)rth ^ kSign;                // L1 = M1 = rth
   const double keep = p.one_minus_omega;
-  f[0] = fma(keep, f[0], fx_to_double((long long)(__umul64hi(uK0, p.fx_c60[0]) - p.fx_d0[0]), p.fx_e[0]));  // x2 = 0
+  out.put(0, fma(keep, f[0], fx_to_double((long long)(__umul64hi(uK0, p.fx_c60[0]) - p.fx_d0[0]), p.fx_e[0])));  // x2 = 0
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
     const long long R0 = (long long)(__umul64hi(uK0, p.fx_c60[k]) + __umul64hi(uK1, p.fx_cx2_59[k]) +
@@ -458,8 +473,7 @@ __device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParam
                                      p.fx_d1[k]);  // Q57
     const long long R2 = (long long)(__umul64hi(uM0, p.fx_c64[k]) + __umul64hi(uTH, p.fx_cx2_60[k]) -
                                      p.fx_d2[k]);  // Q59
-    const u64 R3 = __umul64hi(R, p.fx_c6[k]);   // Q61
-    const u64 R4 = __umul64hi(R, p.fx_c24[k]);  // Q63
+    const u64 R3 = __umul64hi(R, p.fx_c6[k]);  // Q61 of c rho / 6, and Q63 of R4 = c rho / 24
     const int E = p.fx_e[k];
 #pragma unroll
     for (int pr = 0; pr < kPairs; ++pr) {
@@ -468,13 +482,13 @@ __device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParam
       const long long sa = a >> 63;                                      // 0 or -1
       const u64 A = (u64)((a ^ sa) - sa);
       const u64 b = umulhi_t(A, A);                                      // Q60
-      const long long t = R2 + (long long)umulhi_t(b, R4);              // Q59
+      const long long t = R2 + (long long)umulhi_t(b, R3);              // Q59: R2 + b R4
       const long long even = R0 + mulhi_su_t(t, b);                      // Q55
       const long long s = R1 + (long long)umulhi_t(b, R3);              // Q57
       const long long oa = mulhi_su_rn(s, A);                            // Q55: |a| (R1 + b R3)
       const long long odd = (oa ^ sa) - sa;                              // the sign of a
-      f[1 + 2 * pr] = fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E));
-      f[2 + 2 * pr] = fma(keep, f[2 + 2 * pr], fx_to_double(even - odd, E));
+      out.put(1 + 2 * pr, fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E)));
+      out.put(2 + 2 * pr, fma(keep, f[2 + 2 * pr], fx_to_double(even - odd, E)));
     }
   }
 }
@@ -483,8 +497,9 @@ __device__ __forceinline__ void collide_site_fx(double (&f)[kQ], const StepParam
 // u_bar = u + tau g, T_bar = T - tau^2 g^2 / D (Eq. MASTERSHIFT3, Eq. discrete).
 // The equilibrium is evaluated per pair as even +- odd parts with per-shell
 // coefficients (see ShellConsts), pre-scaled by omega rho w_shell.
-__device__ __forceinline__ void collide_site_fp64(double (&f)[kQ], const StepParams& p, double rho, double ux,
-                                                  double uy, double T) {
+template <class O>
+__device__ __forceinline__ void collide_site_fp64(const double (&f)[kQ], const StepParams& p, double rho, double ux,
+                                                  double uy, double T, const O& out) {
   const double ubx = ux;
   const double uby = uy + p.uy_shift;
   const double q = ubx * ubx + uby * uby;
@@ -500,7 +515,7 @@ __device__ __forceinline__ void collide_site_fp64(double (&f)[kQ], const StepPar
   const double keep = p.one_minus_omega;
   {
     const double C0 = A0 + th * (c_shell.alpha[0] + q * c_shell.beta[0] + th * c_shell.gamma[0]);
-    f[0] = fma(keep, f[0], wr * c_shell.w[0] * C0);
+    out.put(0, fma(keep, f[0], wr * c_shell.w[0] * C0));
   }
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
@@ -517,21 +532,22 @@ __device__ __forceinline__ void collide_site_fp64(double (&f)[kQ], const StepPar
       const double b = a * a;
       const double even = P0 + b * (P2 + b * P4);
       const double odd = a * (P1 + b * P3);
-      f[1 + 2 * pr] = fma(keep, f[1 + 2 * pr], even + odd);
-      f[2 + 2 * pr] = fma(keep, f[2 + 2 * pr], even - odd);
+      out.put(1 + 2 * pr, fma(keep, f[1 + 2 * pr], even + odd));
+      out.put(2 + 2 * pr, fma(keep, f[2 + 2 * pr], even - odd));
     }
   }
 }
 
 // One site's collision: moments as exact integer sums, then the fixed-point
-// form inside its ranges, else the FP64 form.
-__device__ __forceinline__ void collide_site(double (&f)[kQ], const StepParams& p) {
+// form inside its ranges, else the FP64 form; the relaxed populations to out.
+template <class O>
+__device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParams& p, const O& out) {
   long long r, jx, jy, e;
   int emax;
   FxSite fs;
   const bool sums = site_sums(f, r, jx, jy, e, emax);
   if (sums && fx_site_from_sums(r, jx, jy, e, emax, p, fs)) {
-    collide_site_fx(f, p, fs);
+    collide_site_fx(f, p, fs, out);
     return;
   }
   double rho, ux, uy, T;
@@ -539,7 +555,11 @@ __device__ __forceinline__ void collide_site(double (&f)[kQ], const StepParams& 
     moments_from_sums(r, jx, jy, e, emax, rho, ux, uy, T);
   else
     site_moments_fp64(f, rho, ux, uy, T);
-  collide_site_fp64(f, p, rho, ux, uy, T);
+  collide_site_fp64(f, p, rho, ux, uy, T, out);
+}
+
+__device__ __forceinline__ void collide_site(double (&f)[kQ], const StepParams& p) {
+  collide_site_to(f, p, InPlace{f});
 }
 
 // Wall bc for a site of a wall band, applied to its gathered populations:
@@ -672,6 +692,31 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) collide_kernel
   store_site<true>(buf, p, x, y, f);
 }
 
+// The halo images of a site whose populations are already in its own
+// element of dst (written by this thread): read back and copied out.
+__device__ __forceinline__ void store_images(double* __restrict__ dst, const StepParams& p, int x, int y) {
+  if (x >= kHx && x < p.Lx - kHx && (!p.periodic_y || (y >= kHx && y < p.Ly - kHx))) return;
+  const char* s = (const char*)(dst + site_index(p, x, y));
+  double f[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(s + p.plane_off[l]);
+  int xs[3] = {x, 0, 0}, ys[3] = {y, 0, 0};
+  int nx = 1, ny = 1;
+  if (x < kHx) xs[nx++] = x + p.Lx;
+  if (x >= p.Lx - kHx) xs[nx++] = x - p.Lx;
+  if (p.periodic_y) {
+    if (y < kHx) ys[ny++] = y + p.Ly;
+    if (y >= p.Ly - kHx) ys[ny++] = y - p.Ly;
+  }
+  for (int a = 0; a < nx; ++a)
+    for (int b = 0; b < ny; ++b) {
+      if (a == 0 && b == 0) continue;  // the site's own element
+      char* d = (char*)(dst + site_index(p, xs[a], ys[b]));
+#pragma unroll
+      for (int l = 0; l < kQ; ++l) *(double*)(d + p.plane_off[l]) = f[l];
+    }
+}
+
 // One site of the fused step: gather (pull), wall bc on the wall bands,
 // collide, store with halo images.
 // p: the lattice (geometry, walls); px: the constants of its collision (tau,
@@ -700,8 +745,14 @@ __device__ __forceinline__ void fused_site(const double* __restrict__ src, doubl
       if (wall ? (cy < -r) : (cy > r)) f[l] = rho_w * p.fw[wall][l];
     }
   }
-  collide_site(f, px);
-  store_site<OFF>(dst, p, x, y, f);
+  if constexpr (OFF) {
+    // each pair straight to the site's planes, then the halo images, if any
+    collide_site_to(f, px, ToPlanes{(char*)(dst + i), p});
+    store_images(dst, p, x, y);
+  } else {
+    collide_site(f, px);
+    store_site<false>(dst, p, x, y, f);
+  }
 }
 
 __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(const double* __restrict__ src, double* __restrict__ dst,

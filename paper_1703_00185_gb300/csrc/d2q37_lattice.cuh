@@ -142,11 +142,11 @@ struct StepParams {
   // Fixed-point equilibrium constants of the FP64 step: per shell k,
   // omega w_k = c_k 2^fx_e[k] with c_k in [0.5, 1); as unsigned integers, each
   // at the scale that puts its product straight into the format it feeds:
-  // c 2^60, 2^62, 2^64; c x2 2^59, 2^60; c x2^2 2^55; (c/6) 2^64; (c/24) 2^66
-  // (x2 = s^2 |c_l|^2).
+  // c 2^60, 2^62, 2^64; c x2 2^59, 2^60; c x2^2 2^55; (c/6) 2^64, which is
+  // also (c/24) 2^66 (x2 = s^2 |c_l|^2).
   unsigned long long fx_c60[kShells], fx_c62[kShells], fx_c64[kShells];
   unsigned long long fx_cx2_59[kShells], fx_cx2_60[kShells], fx_cx4_55[kShells];
-  unsigned long long fx_c6[kShells], fx_c24[kShells];
+  unsigned long long fx_c6[kShells];
   // subtracted from R0, R1, R2 (mod 2^64): y / 2 for each product whose site
   // value enters with its sign bit flipped (x + 2^63), less a rounding
   // correction

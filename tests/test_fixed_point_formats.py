@@ -80,7 +80,8 @@ def shell_consts(s, c2, w, omega):
     c = cw / Fr(2) ** E
     C = dict(E=E, c60=round(c * 2**60), c62=round(c * 2**62), c64=round(c * 2**64),
              cx2_59=round(c * x2 * 2**59), cx2_60=round(c * x2 * 2**60), cx4_55=round(c * x2 * x2 * 2**55),
-             c6=round(c / 6 * 2**64), c24=round(c / 24 * 2**66))
+             c6=round(c / 6 * 2**64))
+    assert C["c6"] == round(c / 24 * 2**66)  # the same integer serves R3 (Q61) and R4 (Q63)
     # y / 2 of each product with a flipped operand, less a rounding correction
     C["d0"] = 0 if c2 == 0 else (C["cx2_59"] >> 1) - 2
     C["d1"] = (C["c62"] >> 1) + (C["cx2_59"] >> 1) - 1
@@ -123,7 +124,7 @@ def equilibrium_fixed(s, shells, wk, R, UX, UY, TH, omega):
         R1 = fits(umulhi(flip(L0), C["c62"]) + umulhi(flip(rth), C["cx2_59"]) - C["d1"], "R1")
         R2 = fits(umulhi(flip(M0), C["c64"]) + umulhi(flip(rth), C["cx2_60"]) - C["d2"], "R2")
         R3 = fits(umulhi(R, C["c6"]), "R3")
-        R4 = fits(umulhi(R, C["c24"]), "R4")
+        R4 = R3  # c rho / 24 at Q63
         for cx, cy in PAIRS:
             if cx * cx + cy * cy != c2:
                 continue
