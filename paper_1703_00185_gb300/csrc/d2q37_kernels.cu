@@ -431,6 +431,11 @@ struct ToPlanes {
   const StepParams& p;  // plane_off
   __device__ __forceinline__ void put(int l, double v) const { *(double*)(d + p.plane_off[l]) = v; }
 };
+struct ToPlanesStride {  // the same with the planes addressed as multiples of the stride
+  double* d;
+  long long plane;
+  __device__ __forceinline__ void put(int l, double v) const { d[l * plane] = v; }
+};
 
 // The collision of collide_site_fp64 below with the equilibrium in fixed
 // point (formats in the comments), for a site inside the fixed-point ranges.
@@ -693,13 +698,16 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) collide_kernel
 }
 
 // The halo images of a site whose populations are already in its own
-// element of dst (written by this thread): read back and copied out.
+// element of dst (written by this thread): read back and copied out.  OFF:
+// the planes addressed with the byte offsets of p (see store_site).
+template <bool OFF>
 __device__ __forceinline__ void store_images(double* __restrict__ dst, const StepParams& p, int x, int y) {
   if (x >= kHx && x < p.Lx - kHx && (!p.periodic_y || (y >= kHx && y < p.Ly - kHx))) return;
-  const char* s = (const char*)(dst + site_index(p, x, y));
+  const double* s = dst + site_index(p, x, y);
   double f[kQ];
 #pragma unroll
-  for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(s + p.plane_off[l]);
+  for (int l = 0; l < kQ; ++l)
+    f[l] = OFF ? *(const double*)((const char*)s + p.plane_off[l]) : s[l * p.plane];
   int xs[3] = {x, 0, 0}, ys[3] = {y, 0, 0};
   int nx = 1, ny = 1;
   if (x < kHx) xs[nx++] = x + p.Lx;
@@ -711,9 +719,14 @@ __device__ __forceinline__ void store_images(double* __restrict__ dst, const Ste
   for (int a = 0; a < nx; ++a)
     for (int b = 0; b < ny; ++b) {
       if (a == 0 && b == 0) continue;  // the site's own element
-      char* d = (char*)(dst + site_index(p, xs[a], ys[b]));
+      double* d = dst + site_index(p, xs[a], ys[b]);
 #pragma unroll
-      for (int l = 0; l < kQ; ++l) *(double*)(d + p.plane_off[l]) = f[l];
+      for (int l = 0; l < kQ; ++l) {
+        if (OFF)
+          *(double*)((char*)d + p.plane_off[l]) = f[l];
+        else
+          d[l * p.plane] = f[l];
+      }
     }
 }
 
@@ -745,14 +758,12 @@ __device__ __forceinline__ void fused_site(const double* __restrict__ src, doubl
       if (wall ? (cy < -r) : (cy > r)) f[l] = rho_w * p.fw[wall][l];
     }
   }
-  if constexpr (OFF) {
-    // each pair straight to the site's planes, then the halo images, if any
+  // each pair straight to the site's planes, then the halo images, if any
+  if constexpr (OFF)
     collide_site_to(f, px, ToPlanes{(char*)(dst + i), p});
-    store_images(dst, p, x, y);
-  } else {
-    collide_site(f, px);
-    store_site<false>(dst, p, x, y, f);
-  }
+  else
+    collide_site_to(f, px, ToPlanesStride{dst + i, p.plane});
+  store_images<OFF>(dst, p, x, y);
 }
 
 __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(const double* __restrict__ src, double* __restrict__ dst,
