@@ -685,18 +685,6 @@ __global__ void __launch_bounds__(128) bc_kernel(const double* __restrict__ src,
   }
 }
 
-__global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) collide_kernel(double* __restrict__ buf, StepParams p) {
-  const int x = blockIdx.x;
-  const int y = blockIdx.y * kBlockY + threadIdx.x;
-  if (y >= p.Ly) return;
-  const char* s = (const char*)(buf + site_index(p, x, y));
-  double f[kQ];
-#pragma unroll
-  for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(s + p.plane_off[l]);
-  collide_site(f, p);
-  store_site<true>(buf, p, x, y, f);
-}
-
 // The halo images of a site whose populations are already in its own
 // element of dst (written by this thread): read back and copied out.  OFF:
 // the planes addressed with the byte offsets of p (see store_site).
@@ -728,6 +716,19 @@ __device__ __forceinline__ void store_images(double* __restrict__ dst, const Ste
           d[l * p.plane] = f[l];
       }
     }
+}
+
+__global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) collide_kernel(double* __restrict__ buf, StepParams p) {
+  const int x = blockIdx.x;
+  const int y = blockIdx.y * kBlockY + threadIdx.x;
+  if (y >= p.Ly) return;
+  double* const b = buf + site_index(p, x, y);
+  double f[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) f[l] = *(const double*)((const char*)b + p.plane_off[l]);
+  // in place: every population is read above before its pair is written back
+  collide_site_to(f, p, ToPlanes{(char*)b, p});
+  store_images<true>(buf, p, x, y);
 }
 
 // One site of the fused step: gather (pull), wall bc on the wall bands,
