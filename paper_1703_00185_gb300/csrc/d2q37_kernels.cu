@@ -17,7 +17,7 @@
 //             Eq. MASTERSHIFT3, in place on dst
 //   fused     propagate + bc + collide in one pass, src -> dst
 //
-// Threads: one per lattice site, blocks of 128 consecutive y of one column
+// Threads: one per lattice site, blocks of 256 consecutive y of one column
 // (the paper's 1-D blocks along y, Sec. "The propagate and bc Kernels").
 // Every warp reads 32 consecutive doubles of each population plane, so each
 // gather is a coalesced 256-byte row shifted by at most 3 elements.
@@ -31,14 +31,14 @@ __constant__ ShellConsts c_shell;
 
 namespace {
 
-constexpr int kBlockY = 128;
+constexpr int kBlockY = 256;
 
 // Minimum resident blocks per SM requested for the FP64 site kernels (caps
-// their registers at 65536 / (128 * blocks)); tuned on GB300: 4 (128
-// registers, no spills) ran the 2048 x 8192 fused step in 3.87 ms against
-// 4.12 ms with 3.
+// their registers at 65536 / (kBlockY * blocks)); tuned on GB300: 2 blocks of
+// 256 (128 registers) ran the 2048 x 8192 fused step in 2.79 ms, against
+// 2.84 ms with 8 of 64, 2.87 ms with 4 of 128 and 3.53 ms with 1 of 512.
 #ifndef D2Q37_SITE_MIN_BLOCKS
-#define D2Q37_SITE_MIN_BLOCKS 4
+#define D2Q37_SITE_MIN_BLOCKS 2
 #endif
 // The batched kernel reads its parameters from memory instead of the
 // constant bank and needs more registers than 128 (it spills 228 bytes per

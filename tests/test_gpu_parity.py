@@ -65,7 +65,7 @@ def pair(Lx, Ly, kernel="separate", **kw):
 
 
 SIZES = [(7, 10, False), (33, 130, False), (256, 128, False), (3, 6, False), (5, 6, True), (17, 40, True),
-         (130, 257, False)]
+         (130, 257, False), (24, 600, False), (9, 520, True)]  # the last three span several 256-row blocks
 
 
 @pytest.mark.parametrize("Lx,Ly,periodic_y", SIZES)
