@@ -288,23 +288,22 @@ __device__ __forceinline__ long long to_fx(double v) {
 // g 2^(E - 55) as an FP64 number, two ways: with the FP64 pipe's 64-bit
 // integer conversion (round to nearest even) and the power of two added to
 // the exponent field, or with integer operations only (round half away from
-// zero).  D2Q37_FX_CVT chooses at build time: 1 on the FP64 pipe (on GB300
-// 4.12 ms per 2048 x 8192 step against 4.37 ms for 0, integer; converting
-// half the populations each way was slower still, 4.65 ms at 4 blocks/SM).
-#ifndef D2Q37_FX_CVT
-#define D2Q37_FX_CVT 1
+// zero).  The shells k >= D2Q37_INT_CVT_SHELL take the integer form (0: all
+// 37 populations, 8: none).  On GB300, with the FP64 pipe about 75 % busy,
+// the last shell's 8 populations that way ran the 2048 x 8192 step in
+// 2.742 ms, against 2.784 ms for none and 2.802 / 2.847 ms for the last two /
+// three shells (all of them, with 4 blocks of 128 per SM: 4.37 against 4.12).
+#ifndef D2Q37_INT_CVT_SHELL
+#define D2Q37_INT_CVT_SHELL 7
 #endif
 
-#if D2Q37_FX_CVT != 0
 // g != 0
 __device__ __forceinline__ double fx_to_double_fp64(long long g, int E) {
   const double d = (double)g;  // exact up to its one rounding
   const u64 bits = (u64)__double_as_longlong(d) + ((u64)(long long)(E - kFxOut) << 52);
   return __longlong_as_double((long long)bits);
 }
-#endif
 
-#if D2Q37_FX_CVT == 0
 // |g| < 2^32 (including 0): the general normalisation
 __device__ __noinline__ double fx_to_double_small(u64 m, int E, u64 sign) {
   if (!m) return 0.0;
@@ -330,17 +329,13 @@ __device__ __forceinline__ double fx_to_double_int(long long g, int E) {
   const u64 bits = ((u64)(long long)(1023 + 62 - kFxOut + E - lz) << 52) + mant;
   return __longlong_as_double((long long)(bits | sign));
 }
-#endif
 
-// The lowest bit of g is set first: g is never zero (which the exponent add
-// of the FP64 form needs), and it is 0.5 larger on average, which the
-// per-shell corrections of the equilibrium take into account.
-__device__ __forceinline__ double fx_to_double(long long g, int E) {
-#if D2Q37_FX_CVT == 0
-  return fx_to_double_int(g | 1, E);
-#else
-  return fx_to_double_fp64(g | 1, E);
-#endif
+// The population of shell k.  The lowest bit of g is set first: g is never
+// zero (which the exponent add of the FP64 form needs), and it is 0.5 larger
+// on average, which the per-shell corrections of the equilibrium take into
+// account.
+__device__ __forceinline__ double fx_to_double(long long g, int E, int k) {
+  return k >= D2Q37_INT_CVT_SHELL ? fx_to_double_int(g | 1, E) : fx_to_double_fp64(g | 1, E);
 }
 
 // c v for a hop component c in -3..3 given the multiples m = {v, 2v, 3v}.
@@ -469,7 +464,7 @@ __device__ __forceinline__ void collide_site_fx(const double (&f)[kQ], const Ste
   const u64 uK0 = (u64)K0, uK1 = (u64)K1 ^ kSign, uL0 = (u64)L0 ^ kSign;  // x + 2^63
   const u64 uM0 = (u64)M0 ^ kSign, uTH = (u64)rth ^ kSign;                // L1 = M1 = rth
   const double keep = p.one_minus_omega;
-  out.put(0, fma(keep, f[0], fx_to_double((long long)(__umul64hi(uK0, p.fx_c60[0]) - p.fx_d0[0]), p.fx_e[0])));  // x2 = 0
+  out.put(0, fma(keep, f[0], fx_to_double((long long)(__umul64hi(uK0, p.fx_c60[0]) - p.fx_d0[0]), p.fx_e[0], 0)));  // x2 = 0
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
     const long long R0 = (long long)(__umul64hi(uK0, p.fx_c60[k]) + __umul64hi(uK1, p.fx_cx2_59[k]) +
@@ -492,8 +487,8 @@ __device__ __forceinline__ void collide_site_fx(const double (&f)[kQ], const Ste
       const long long s = R1 + (long long)umulhi_t(b, R3);              // Q57
       const long long oa = mulhi_su_rn(s, A);                            // Q55: |a| (R1 + b R3)
       const long long odd = (oa ^ sa) - sa;                              // the sign of a
-      out.put(1 + 2 * pr, fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E)));
-      out.put(2 + 2 * pr, fma(keep, f[2 + 2 * pr], fx_to_double(even - odd, E)));
+      out.put(1 + 2 * pr, fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E, k)));
+      out.put(2 + 2 * pr, fma(keep, f[2 + 2 * pr], fx_to_double(even - odd, E, k)));
     }
   }
 }
