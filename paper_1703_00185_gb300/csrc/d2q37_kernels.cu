@@ -288,13 +288,14 @@ __device__ __forceinline__ long long to_fx(double v) {
 // g 2^(E - 55) as an FP64 number, two ways: with the FP64 pipe's 64-bit
 // integer conversion (round to nearest even) and the power of two added to
 // the exponent field, or with integer operations only (round half away from
-// zero).  The shells k >= D2Q37_INT_CVT_SHELL take the integer form (0: all
-// 37 populations, 8: none).  On GB300, with the FP64 pipe about 75 % busy,
-// the last shell's 8 populations that way ran the 2048 x 8192 step in
-// 2.742 ms, against 2.784 ms for none and 2.802 / 2.847 ms for the last two /
-// three shells (all of them, with 4 blocks of 128 per SM: 4.37 against 4.12).
-#ifndef D2Q37_INT_CVT_SHELL
-#define D2Q37_INT_CVT_SHELL 7
+// zero).  The shells k whose bit is set in D2Q37_INT_CVT_MASK take the
+// integer form.  On GB300, with the FP64 pipe about 75 % busy, the last
+// shell's 8 populations that way (0x80) ran the 2048 x 8192 step in 2.742 ms,
+// against 2.784 ms for none, 2.802 / 2.847 ms for the last two / three
+// shells and 2.74-2.82 ms for shell 7 with one of shells 1, 3, 4, 5 (all of
+// them, with 4 blocks of 128 per SM: 4.37 against 4.12).
+#ifndef D2Q37_INT_CVT_MASK
+#define D2Q37_INT_CVT_MASK 0x80
 #endif
 
 // g != 0
@@ -335,7 +336,7 @@ __device__ __forceinline__ double fx_to_double_int(long long g, int E) {
 // on average, which the per-shell corrections of the equilibrium take into
 // account.
 __device__ __forceinline__ double fx_to_double(long long g, int E, int k) {
-  return k >= D2Q37_INT_CVT_SHELL ? fx_to_double_int(g | 1, E) : fx_to_double_fp64(g | 1, E);
+  return ((D2Q37_INT_CVT_MASK >> k) & 1) ? fx_to_double_int(g | 1, E) : fx_to_double_fp64(g | 1, E);
 }
 
 // c v for a hop component c in -3..3 given the multiples m = {v, 2v, 3v}.
