@@ -31,11 +31,9 @@ METRIC = "MLUPS per step"
 UNIT = "MLUPS"
 # algorithmic bytes per site update: 37 populations read + 37 written
 BYTES_PER_SITE = {"fp64": 592, "fp32": 296, "fp32-df": 296}
-# FP64 work of the fused kernel per site, from its ncu instruction counters:
-# 17.15 DADD + 106.06 DMUL + 178.00 DFMA = 301.2 FP64 instructions, 479.2 flop
 # FP64-pipe instructions per site of the fused FP64 kernel (ncu on 2048 x 1024:
-# DFMA + DMUL + DADD + the integer-to-FP64 conversions)
-FP64_PIPE_INST_PER_SITE = 79.6
+# 37 DFMA + 29 integer-to-FP64 conversions + 3.2 DADD + 2.4 DMUL)
+FP64_PIPE_INST_PER_SITE = 71.6
 # FP64 pipe peak from unit counts and clocks: 2 FP64 instructions per SM per
 # clock (ncu: ...dfma_pred_on.avg.peak_sustained = 2) x 152 SMs x 2.07 GHz
 FP64_PEAK_GINST = 2 * 152 * 2.07
@@ -45,8 +43,8 @@ FP64_PEAK_GINST = 2 * 152 * 2.07
 ORACLE_FLOPS_PER_SITE = 42640
 ORACLE_NONTRIVIAL_FLOPS_PER_SITE = 17477
 # DRAM bytes per fused launch at 2048 x 8192, scaled by sites from the ncu
-# capture of the same kernel on 2048 x 1024 (1257.3 MB per launch there)
-FUSED_TRAFFIC_BYTES_2048x8192 = 1257.3e6 * 8
+# capture of the same kernel on 2048 x 1024 (1231.4 MB per launch there)
+FUSED_TRAFFIC_BYTES_2048x8192 = 1231.4e6 * 8
 # the same for the FP32-storage double-float kernel, from its capture on
 # 2048 x 2048 (1273.0 MB per launch there)
 FUSED32_DF_TRAFFIC_BYTES_2048x8192 = 1273.0e6 * 4
