@@ -171,9 +171,11 @@ void lbm_destroy(lbm_t* h);
  * single-GPU form for many independent jobs.  Every lattice keeps its own
  * memory, parameters and state (its lbm_t); the batch advances all of them by
  * one step per launch of a grid-stride fused kernel over tiles (one column by
- * block_y rows) of every lattice, and lbm_batch_step(n >= 4) replays a
- * captured two-step CUDA graph.  Per-site arithmetic is the fused kernel's,
- * so a lattice's result is the same batched or alone. */
+ * block_y rows) of every lattice, or (block_y = 0) by one launch of the
+ * single-lattice fused kernel per lattice, spread over four streams forked
+ * from the batch stream and joined back to it; lbm_batch_step(n >= 4)
+ * replays a captured two-step CUDA graph.  Per-site arithmetic is the fused
+ * kernel's, so a lattice's result is the same batched or alone. */
 typedef struct lbm_batch_t lbm_batch_t;
 
 /* Group n lattices (same precision, each with a state) on cuda_stream (NULL:
@@ -188,11 +190,14 @@ int lbm_batch_step(lbm_batch_t* b, int n);
 
 /* Launch shape: block_y in {64, 128, 256} rows per tile; blocks_per_sm 0 for
  * one block per tile, else a persistent grid of blocks_per_sm x SM count
- * (at most the kernel's occupancy; LBM_EINVAL otherwise). */
+ * (at most the kernel's occupancy; LBM_EINVAL otherwise).  block_y = 0 with
+ * blocks_per_sm = 0: one single-lattice launch per lattice and step (n
+ * launches per step, counted by lbm_batch_launch_count). */
 int lbm_batch_set_config(lbm_batch_t* b, int block_y, int blocks_per_sm);
 int lbm_batch_get_config(const lbm_batch_t* b, int* block_y, int* blocks_per_sm);
 
-/* Time every launch shape over trial_steps launches and keep the fastest;
+/* Time every launch shape (block_y = 0 included) over trial_steps launches
+ * and keep the fastest;
  * the trials recompute the same step, so the lattices' state does not
  * advance.  Outputs (any may be NULL): the chosen shape and its ms per step.
  * Synchronises the batch stream. */

@@ -1,12 +1,16 @@
-// Batched stepping of many independent lattices in one launch per step
-// (C ABI declared in include/d2q37.h, lbm_batch_*).
+// Batched stepping of many independent lattices (C ABI declared in
+// include/d2q37.h, lbm_batch_*).
 //
 // The lattices keep their own memory and parameters (lbm_t handles); the
 // batch owns a device table of BatchEntry (parameters, both buffers, the
 // buffer holding the state, tile range) and advances every lattice by one
 // step per launch of the batched fused kernel, walking the tiles of all
-// lattices with a grid-stride loop.  lbm_batch_step(n) replays a captured
-// two-step CUDA graph when the stream can be captured.
+// lattices with a grid-stride loop.  Launch shape block_y = 0 instead issues
+// the single-lattice fused kernel once per lattice (its parameters in the
+// constant bank), spread over kAux streams forked from and joined to the
+// batch stream, so that small lattices run side by side.
+// lbm_batch_step(n) replays a captured two-step CUDA graph when the stream
+// can be captured (with block_y = 0 a graph of parallel branches).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -33,7 +37,14 @@ struct lbm_batch_t {
   int64_t launches;
   cudaGraphExec_t graph2;  // two steps from parity 0
   int graph_config;        // block_y * 16 + blocks_per_sm the graph was captured with
+  int64_t graph_launches;  // kernels in graph2 (2, or 2 n with block_y = 0)
   bool graph_unavailable;
+  // block_y = 0: one launch per lattice, largest first, round robin over aux
+  static constexpr int kAux = 4;
+  cudaStream_t aux[kAux];
+  cudaEvent_t fork, join[kAux];
+  bool aux_ready;
+  std::vector<int> order;  // lattices by decreasing site count
 };
 
 namespace {
@@ -41,6 +52,50 @@ namespace {
 int check(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ECUDA; }
 
 int slot_of(int block_y) { return block_y == 64 ? 0 : block_y == 128 ? 1 : block_y == 256 ? 2 : -1; }
+
+// The streams and events of the per-lattice form (made when the batch is).
+int ensure_aux(lbm_batch_t* b) {
+  if (b->aux_ready) return LBM_OK;
+  bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < lbm_batch_t::kAux; ++k) {
+    b->aux[k] = nullptr;
+    b->join[k] = nullptr;
+    ok = ok && cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+  }
+  b->aux_ready = true;  // destroy releases whatever was made
+  if (!ok) {
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  return LBM_OK;
+}
+
+// One step of every lattice with its own fused kernel: forked from the batch
+// stream onto the aux streams and joined back to it.
+int launch_each(lbm_batch_t* b, int parity) {
+  int rc = ensure_aux(b);
+  if (rc) return rc;
+  rc = check(cudaEventRecord(b->fork, b->stream));
+  for (int k = 0; k < lbm_batch_t::kAux && !rc; ++k) rc = check(cudaStreamWaitEvent(b->aux[k], b->fork, 0));
+  for (size_t j = 0; j < b->order.size() && !rc; ++j) {
+    const int i = b->order[j];
+    const lbm_t* h = b->lat[i];
+    const int c = b->host_tab[0][i].cur ^ parity;
+    cudaStream_t s = b->aux[j % lbm_batch_t::kAux];
+    const int n = b->prec == LBM_PRECISION_FP64
+                      ? launch_fused((const double*)h->buf[c], (double*)h->buf[c ^ 1], h->sp, s)
+                      : launch_fused32((const float*)h->buf[c], (float*)h->buf[c ^ 1], h->sp,
+                                       b->prec == LBM_PRECISION_FP32_FP64, s);
+    if (n < 0) rc = LBM_ECUDA;
+    else b->launches += n;
+  }
+  for (int k = 0; k < lbm_batch_t::kAux && !rc; ++k) {
+    rc = check(cudaEventRecord(b->join[k], b->aux[k]));
+    if (!rc) rc = check(cudaStreamWaitEvent(b->stream, b->join[k], 0));
+  }
+  return rc;
+}
 
 int max_blocks_per_sm(const lbm_batch_t* b, int block_y) {
   return b->prec == LBM_PRECISION_FP64 ? batch_blocks_per_sm(block_y)
@@ -55,6 +110,7 @@ long long grid_of(const lbm_batch_t* b, int block_y, int blocks_per_sm) {
 }
 
 int launch(lbm_batch_t* b, int block_y, int blocks_per_sm, int parity) {
+  if (block_y == 0) return launch_each(b, parity);
   const int s = slot_of(block_y);
   const int grid = (int)grid_of(b, block_y, blocks_per_sm);
   const int n = b->prec == LBM_PRECISION_FP64
@@ -89,6 +145,7 @@ bool pair_graph(lbm_batch_t* b, cudaGraphExec_t* out) {
     const int64_t before = b->launches;
     const int r0 = launch(b, b->block_y, b->blocks_per_sm, 0);
     const int r1 = launch(b, b->block_y, b->blocks_per_sm, 1);
+    b->graph_launches = b->launches - before;
     b->launches = before;
     const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || r0 || r1 || cudaGraphInstantiate(&b->graph2, g, 0) != cudaSuccess) {
@@ -187,12 +244,24 @@ int lbm_batch_create(int n, lbm_t* const* lattices, void* cuda_stream, lbm_batch
     lbm_batch_destroy(b);
     return rc;
   }
+  // the per-lattice form's streams now, never inside a stream capture
+  rc = ensure_aux(b);
+  if (rc) {
+    lbm_batch_destroy(b);
+    return rc;
+  }
+  b->order.resize(n);
+  for (int i = 0; i < n; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int i, int j) {
+    return (long long)lattices[i]->Lx * lattices[i]->Ly > (long long)lattices[j]->Lx * lattices[j]->Ly;
+  });
   *out = b;
   return LBM_OK;
 }
 
 int lbm_batch_set_config(lbm_batch_t* b, int block_y, int blocks_per_sm) {
-  if (!b || slot_of(block_y) < 0 || blocks_per_sm < 0) return LBM_EINVAL;
+  if (!b || blocks_per_sm < 0) return LBM_EINVAL;
+  if (block_y == 0 ? blocks_per_sm != 0 : slot_of(block_y) < 0) return LBM_EINVAL;
   if (blocks_per_sm > 0 && blocks_per_sm > max_blocks_per_sm(b, block_y)) return LBM_EINVAL;
   b->block_y = block_y;
   b->blocks_per_sm = blocks_per_sm;
@@ -219,7 +288,7 @@ int lbm_batch_step(lbm_batch_t* b, int n) {
     cudaGraphExec_t g;
     while (n - t >= 2 && pair_graph(b, &g)) {
       if (cudaGraphLaunch(g, b->stream) != cudaSuccess) return LBM_ECUDA;
-      b->launches += 2;
+      b->launches += b->graph_launches;
       t += 2;
     }
   }
@@ -243,10 +312,10 @@ int lbm_batch_autotune(lbm_batch_t* b, int trial_steps, int* block_y, int* block
   int rc = LBM_OK;
   float best = 1e30f;
   int best_by = b->block_y, best_bps = b->blocks_per_sm;
-  const int bys[3] = {64, 128, 256};
+  const int bys[4] = {64, 128, 256, 0};  // 0: one launch per lattice
   const int64_t launches0 = b->launches;
-  for (int s = 0; s < 3 && !rc; ++s) {
-    const int occ = max_blocks_per_sm(b, bys[s]);
+  for (int s = 0; s < 4 && !rc; ++s) {
+    const int occ = bys[s] ? max_blocks_per_sm(b, bys[s]) : 0;
     for (int bps = 0; bps <= occ && !rc; ++bps) {
       // the same parity every launch: each trial recomputes the same step into
       // the other buffer, so the lattices' state does not advance
@@ -287,6 +356,16 @@ void lbm_batch_destroy(lbm_batch_t* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->graph2) cudaGraphExecDestroy(b->graph2);
+  if (b->aux_ready) {
+    for (int k = 0; k < lbm_batch_t::kAux; ++k) {
+      if (b->aux[k]) {
+        cudaStreamSynchronize(b->aux[k]);
+        cudaStreamDestroy(b->aux[k]);
+      }
+      if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+  }
   for (BatchEntry* t : b->dev_tab)
     if (t) cudaFree(t);
   for (int* t : b->dev_tile_entry)

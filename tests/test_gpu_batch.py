@@ -1,6 +1,7 @@
-"""GPU checks of batched stepping (many lattices, one launch per step),
-through the C ABI: each lattice's result is bit-identical to the same lattice
-stepped alone, for every launch shape, and autotuning leaves the state alone."""
+"""GPU checks of batched stepping (many lattices, one launch per step, or one
+launch per lattice in concurrent branches), through the C ABI: each
+lattice's result is bit-identical to the same lattice stepped alone, for
+every launch shape, and autotuning leaves the state alone."""
 import numpy as np
 import pytest
 
@@ -36,7 +37,7 @@ def make(precision, periodic_last=True, shared_tau=False):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32-df"])
-@pytest.mark.parametrize("config", [(128, 0), (64, 2), (256, 1)])
+@pytest.mark.parametrize("config", [(128, 0), (64, 2), (256, 1), (0, 0)])
 @pytest.mark.parametrize("shared_tau", [False, True])
 def test_batch_equals_alone(precision, config, shared_tau):
     alone, batched = make(precision, shared_tau=shared_tau), make(precision, shared_tau=shared_tau)
@@ -46,7 +47,7 @@ def test_batch_equals_alone(precision, config, shared_tau):
     b.set_config(*config)
     b.step(7)
     b.synchronize()
-    assert b.launch_count == 7
+    assert b.launch_count == (7 if config[0] else 7 * len(SIZES))  # block_y 0: a launch per lattice
     for a, c in zip(alone, batched):
         assert np.array_equal(a.populations(), c.populations())
     # and the lattices continue correctly on their own handles afterwards
@@ -86,3 +87,5 @@ def test_batch_rejects_bad_input():
     b = lbm.Batch([a])
     with pytest.raises(lbm.LBMError):
         b.set_config(96, 0)
+    with pytest.raises(lbm.LBMError):
+        b.set_config(0, 1)  # the per-lattice form has no persistent grid
