@@ -221,7 +221,7 @@ void lbm_batch_destroy(lbm_batch_t* b);
  * steps, one batched fused launch per step on cuda_stream, exactly as
  * lbm_batch_step with tiles of 128 rows.  It allocates no device memory and
  * calls no allocating library routine: its tile table lives in a file-scope
- * static device array of LBM_STATIC_BATCH_MAX entries (about 450 KB) that
+ * static device array of LBM_STATIC_BATCH_MAX entries (about 680 KB) that
  * every GPU loading this library holds until the process exits.
  *  - n > LBM_STATIC_BATCH_MAX returns LBM_ETOOBIG and does nothing.
  *  - The first call on a device looks up the array's device address
@@ -244,9 +244,10 @@ int lbm_batch_step_static(int n, lbm_t* const* lattices, int steps, void* cuda_s
  * (lbm_required_bytes) fits in the free part of one pre-allocated pool of
  * hbm_budget_bytes.  Each lbm_server_tick admits what fits, advances every
  * admitted job by k = min(max_steps_per_tick, fewest steps left) steps with
- * one batched fused launch per step and precision group (each group on its
- * own stream, so their work overlaps), then copies the fields of jobs that
- * reached their step count to host memory and frees their device memory.
+ * its fused kernel, once per step on the job's stream (one of four, assigned
+ * at admission to the one with the fewest active sites, so that the jobs run
+ * side by side), then copies the fields of jobs that reached their step
+ * count to host memory and frees their device memory.
  * All calls are from one host thread; a tick synchronises its streams. */
 typedef struct lbm_server_t lbm_server_t;
 
