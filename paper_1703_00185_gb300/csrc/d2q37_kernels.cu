@@ -10,7 +10,7 @@
 //   wrap      pbc: fill the 3-column x halos (and y halos when y is periodic);
 //             needed only after a state is uploaded or after a propagate
 //             without collide, because collide and fused write the halo
-//             images of the edge columns themselves (store_site)
+//             images of the edge columns themselves (store_images)
 //   propagate pull form of Eq. master2: dst_l(x,y) = src_l(x - c_lx, y - c_ly)
 //   bc        diffuse walls on rows 0..2 and Ly-3..Ly-1
 //   collide   BGK relaxation (Eq. discrete) to the shifted equilibrium of
@@ -415,13 +415,9 @@ __device__ __forceinline__ bool fx_site_from_sums(long long r, long long jx, lon
   return true;
 }
 
-// Where a collision puts the relaxed populations: back into the site's
-// register array, or straight into the site's planes of the destination, so
-// that each pair's registers are free once it is relaxed.
-struct InPlace {
-  double (&f)[kQ];
-  __device__ __forceinline__ void put(int l, double v) const { f[l] = v; }
-};
+// Where a collision puts the relaxed populations: straight into the site's
+// planes of the destination, so that each pair's registers are free once it
+// is relaxed.
 struct ToPlanes {
   char* d;              // the site's element of plane 0
   const StepParams& p;  // plane_off
@@ -559,10 +555,6 @@ __device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParam
   collide_site_fp64(f, p, rho, ux, uy, T, out);
 }
 
-__device__ __forceinline__ void collide_site(double (&f)[kQ], const StepParams& p) {
-  collide_site_to(f, p, InPlace{f});
-}
-
 // Wall bc for a site of a wall band, applied to its gathered populations:
 // rows r = 0..2 from the wall; a population is missing when the pull took it
 // from beyond the wall, outgoing when it leaves the column past the wall.
@@ -590,39 +582,6 @@ __device__ __forceinline__ double wall_density(const double* __restrict__ src, c
 // (the pbc step folded into the writer; the halo columns see the same values
 // the wrap kernel would copy).  x is uniform across a block, so the extra
 // stores are divergence-free except on periodic y edges.
-// OFF: address the planes with the byte offsets of p (read from the constant
-// bank by the single-lattice kernels) instead of multiples of p.plane.
-template <bool OFF = false>
-__device__ __forceinline__ void store_site(double* __restrict__ dst, const StepParams& p, int x, int y,
-                                           const double (&f)[kQ]) {
-  if (x >= kHx && x < p.Lx - kHx && (!p.periodic_y || (y >= kHx && y < p.Ly - kHx))) {
-    const long long i = site_index(p, x, y);  // no halo image: the common case
-    if constexpr (OFF) {
-      char* d = (char*)(dst + i);
-#pragma unroll
-      for (int l = 0; l < kQ; ++l) *(double*)(d + p.plane_off[l]) = f[l];
-    } else {
-#pragma unroll
-      for (int l = 0; l < kQ; ++l) dst[l * p.plane + i] = f[l];
-    }
-    return;
-  }
-  int xs[3] = {x, 0, 0}, ys[3] = {y, 0, 0};
-  int nx = 1, ny = 1;
-  if (x < kHx) xs[nx++] = x + p.Lx;
-  if (x >= p.Lx - kHx) xs[nx++] = x - p.Lx;
-  if (p.periodic_y) {
-    if (y < kHx) ys[ny++] = y + p.Ly;
-    if (y >= p.Ly - kHx) ys[ny++] = y - p.Ly;
-  }
-  for (int a = 0; a < nx; ++a)
-    for (int b = 0; b < ny; ++b) {
-      const long long i = site_index(p, xs[a], ys[b]);
-#pragma unroll
-      for (int l = 0; l < kQ; ++l) dst[l * p.plane + i] = f[l];
-    }
-}
-
 __global__ void __launch_bounds__(256) wrap_kernel(double* __restrict__ buf, StepParams p) {
   const int rows_a = p.periodic_y ? p.Ly + 2 * kHx : p.Ly;
   const int y0 = p.periodic_y ? -kHx : 0;
@@ -683,7 +642,8 @@ __global__ void __launch_bounds__(128) bc_kernel(const double* __restrict__ src,
 
 // The halo images of a site whose populations are already in its own
 // element of dst (written by this thread): read back and copied out.  OFF:
-// the planes addressed with the byte offsets of p (see store_site).
+// the planes addressed with the byte offsets of p (read from the constant
+// bank by the single-lattice kernels) instead of multiples of p.plane.
 template <bool OFF>
 __device__ __forceinline__ void store_images(double* __restrict__ dst, const StepParams& p, int x, int y) {
   if (x >= kHx && x < p.Lx - kHx && (!p.periodic_y || (y >= kHx && y < p.Ly - kHx))) return;
@@ -731,7 +691,7 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) collide_kernel
 // collide, store with halo images.
 // p: the lattice (geometry, walls); px: the constants of its collision (tau,
 // g: the fixed-point tables, omega, the field shifts), the same object for a
-// single lattice.  OFF: addresses from the byte offsets of p (see store_site).
+// single lattice.  OFF: addresses from the byte offsets of p (see store_images).
 template <bool OFF>
 __device__ __forceinline__ void fused_site(const double* __restrict__ src, double* __restrict__ dst,
                                            const StepParams& p, const StepParams& px, int x, int y) {
