@@ -385,6 +385,7 @@ bool fused_pair_graph(lbm_t* h, cudaGraphExec_t* out) {
       return false;
     }
     cudaGraphDestroy(graph);
+    h->graph2_launches = n1 + n2;
   }
   *out = g;
   return true;
@@ -589,7 +590,7 @@ int lbm_step(lbm_t* h, int n) {
     cudaGraphExec_t g;
     while (n - t >= 2 && fused_pair_graph(h, &g)) {
       if (cudaGraphLaunch(g, h->stream) != cudaSuccess) return LBM_ECUDA;
-      h->launches += 2;
+      h->launches += h->graph2_launches;
       t += 2;  // two swaps: the current buffer is unchanged
     }
   }

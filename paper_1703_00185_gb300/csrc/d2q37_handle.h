@@ -28,6 +28,7 @@ struct lbm_t {
   bool halo_valid;  // halo columns (and rows, if y is periodic) mirror the current state
   int64_t launches;
   cudaGraphExec_t graph2[2];  // two fused steps starting from buffer 0 / 1
+  int64_t graph2_launches;  // kernels in one replay of graph2 (2 steps)
   bool graph_unavailable;
   // per-kernel timing: event pairs recorded around launches, folded into the
   // totals when the stream is synchronised

@@ -32,6 +32,7 @@ __constant__ ShellConsts c_shell;
 namespace {
 
 constexpr int kBlockY = 256;
+constexpr int kWallBlock = 128;
 
 // Minimum resident blocks per SM requested for the FP64 site kernels (caps
 // their registers at 65536 / (kBlockY * blocks)); tuned on GB300: 2 blocks of
@@ -692,7 +693,8 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) collide_kernel
 // p: the lattice (geometry, walls); px: the constants of its collision (tau,
 // g: the fixed-point tables, omega, the field shifts), the same object for a
 // single lattice.  OFF: addresses from the byte offsets of p (see store_images).
-template <bool OFF>
+// WALLS = false: the caller never passes a wall-band site.
+template <bool OFF, bool WALLS = true>
 __device__ __forceinline__ void fused_site(const double* __restrict__ src, double* __restrict__ dst,
                                            const StepParams& p, const StepParams& px, int x, int y) {
   const long long i = site_index(p, x, y);
@@ -705,7 +707,7 @@ __device__ __forceinline__ void fused_site(const double* __restrict__ src, doubl
 #pragma unroll
     for (int l = 0; l < kQ; ++l) f[l] = src[l * p.plane + i - vel_cx(l) * p.NY - vel_cy(l)];
   }
-  if (!p.periodic_y && (y < 3 || y >= p.Ly - 3)) {
+  if (WALLS && !p.periodic_y && (y < 3 || y >= p.Ly - 3)) {
     const int wall = y >= p.Ly - 3;
     const int r = wall ? p.Ly - 1 - y : y;
     const double rho_w = wall_density(src, p, x, wall);
@@ -728,7 +730,20 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(c
   const int x = blockIdx.x;
   const int y = blockIdx.y * kBlockY + threadIdx.x;
   if (y >= p.Ly) return;
-  fused_site<true>(src, dst, p, p, x, y);
+  if (!p.periodic_y && (y < 3 || y >= p.Ly - 3)) return;  // wall_band_kernel's
+  fused_site<true, false>(src, dst, p, p, x, y);
+}
+
+// The fused step of the six wall-band rows of every column (y = 0..2 and
+// Ly - 3..Ly - 1, walls only): packed 32 sites to a warp, so that the wall
+// bc's work runs in full warps instead of in three lanes of a fused_kernel
+// warp (a warp holding wall rows cost about three ordinary warps there).
+__global__ void __launch_bounds__(kWallBlock) wall_band_kernel(const double* __restrict__ src,
+                                                              double* __restrict__ dst, StepParams p) {
+  const int t = blockIdx.x * kWallBlock + threadIdx.x;
+  if (t >= 6 * p.Lx) return;
+  const int x = t / 6, k = t - 6 * x;
+  fused_site<true, true>(src, dst, p, p, x, k < 3 ? k : p.Ly - 6 + k);
 }
 
 // Many lattices in one launch: block-sized tiles (one column x, BY
@@ -836,7 +851,9 @@ int launch_collide(double* buf, const StepParams& p, cudaStream_t stream) {
 
 int launch_fused(const double* src, double* dst, const StepParams& p, cudaStream_t stream) {
   fused_kernel<<<site_grid(p), kBlockY, 0, stream>>>(src, dst, p);
-  return done(1);
+  if (p.periodic_y) return done(1);
+  wall_band_kernel<<<(6 * p.Lx + kWallBlock - 1) / kWallBlock, kWallBlock, 0, stream>>>(src, dst, p);
+  return done(2);
 }
 
 template <int BY>

@@ -47,7 +47,10 @@ def test_batch_equals_alone(precision, config, shared_tau):
     b.set_config(*config)
     b.step(7)
     b.synchronize()
-    assert b.launch_count == (7 if config[0] else 7 * len(SIZES))  # block_y 0: a launch per lattice
+    # block_y 0: each lattice's fused step, in FP64 two kernels with walls (sites, wall bands)
+    per_step = 1 if config[0] else sum(2 if precision == "fp64" and not lat.params.periodic_y else 1
+                                       for lat in batched)
+    assert b.launch_count == 7 * per_step
     for a, c in zip(alone, batched):
         assert np.array_equal(a.populations(), c.populations())
     # and the lattices continue correctly on their own handles afterwards

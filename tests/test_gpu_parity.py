@@ -136,7 +136,8 @@ def test_full_step_256x128_100_steps(kernel, c1_reference):
     n0 = g.launch_count
     g.step(100)
     # one pbc launch after the upload, then the writers keep the halos filled
-    assert g.launch_count - n0 == 1 + (1 if kernel == "fused" else 3) * 100
+    # fused: the sites' and the wall bands' kernels; separate: propagate, bc, collide
+    assert g.launch_count - n0 == 1 + (2 if kernel == "fused" else 3) * 100
     errs = rel_field_errors(g.fields(), c1_reference)
     assert max(errs) <= FIELD_TOL, errs
 
@@ -184,7 +185,7 @@ def test_graph_replay_matches_single_steps():
     a.step(11)
     for _ in range(11):
         b.step(1)
-    assert a.launch_count - n0 == 12
+    assert a.launch_count - n0 == 1 + 11 * 2  # pbc, then two kernels per step
     assert np.array_equal(a.populations(), b.populations())
 
 
@@ -222,7 +223,11 @@ def test_errors_and_edge_cases():
     lbm.lbm_init_rayleigh_taylor(h, 1)
     lbm.lbm_step(h, 3)
     lbm.lbm_synchronize(h)
-    assert lbm.lbm_launch_count(h) == 1 + 1 + 3  # init, pbc, 3 fused steps
+    # init, pbc, 3 fused steps of two kernels (the sites and the wall bands)
+    assert lbm.lbm_launch_count(h) == 1 + 1 + 3 * 2
+    lbm.lbm_step(h, 6)  # replayed two-step graphs count their kernels too
+    lbm.lbm_synchronize(h)
+    assert lbm.lbm_launch_count(h) == 1 + 1 + 9 * 2
     lbm.lbm_destroy(h)
 
 
