@@ -264,7 +264,7 @@ def roofline_of(kind, avg_s, sites, precision, traffic=None):
                           "peak": round(FP64_PEAK_GINST, 2), "unit": "G FP64-pipe instructions/s",
                           "frac": round(ginst / FP64_PEAK_GINST, 4),
                           "peak_source": "derived: 2 FP64-pipe instructions/clk/SM x 152 SMs x 2.07 GHz"}
-    r["avg_launch_ms"] = round(avg_s * 1e3, 4)
+    r["avg_launch_ms"] = round(avg_s * 1e3, 4)  # per call of the step's launcher (one step)
     return r
 
 
@@ -415,7 +415,10 @@ def run_ours(a):
     kind = max(kt, key=lambda k: kt[k][0])
     traffic = FUSED_TRAFFIC_BYTES_2048x8192 if (kind == "fused" and a.precision == "fp64" and
                                                  (a.Lx, a.Ly) == (2048, 8192)) else None
-    roofline = roofline_of(kind, kt[kind][0] / kt[kind][1] * 1e-3, sites, a.precision, traffic)
+    # per step: the library times each launcher call, and the fused FP64 step is
+    # two kernels (the sites, then the wall-band rows of walled lattices)
+    roofline = roofline_of(kind, kt[kind][0] / a.steps * 1e-3, sites, a.precision, traffic)
+    roofline["kernels_per_step"] = round(kt[kind][1] / a.steps, 3)
 
     # end to end through the C ABI with pinned host buffers: upload state, one step, read fields
     e2e = None
@@ -458,7 +461,7 @@ def run_ours(a):
             errs = [float(np.linalg.norm(x - y) / np.linalg.norm(y)) for x, y in zip(fields, ref_fields)]
             forms[prec] = {"value": round(sites * a.steps / (fms * 1e-3) / 1e6, 3), "unit": UNIT,
                            "ms_per_step": round(fms / a.steps, 4), "dtype": DTYPES[prec],
-                           "roofline": roofline_of(fkind, fkt[fkind][0] / fkt[fkind][1] * 1e-3, sites, prec,
+                           "roofline": roofline_of(fkind, fkt[fkind][0] / a.steps * 1e-3, sites, prec,
                                                    FUSED32_DF_TRAFFIC_BYTES_2048x8192
                                                    if (fkind == "fused" and prec == "fp32-df" and
                                                        (a.Lx, a.Ly) == (2048, 8192)) else None),
