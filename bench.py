@@ -31,10 +31,10 @@ METRIC = "MLUPS per step"
 UNIT = "MLUPS"
 # algorithmic bytes per site update: 37 populations read + 37 written
 BYTES_PER_SITE = {"fp64": 592, "fp32": 296, "fp32-df": 296}
-# FP64-pipe instructions per site of the fused FP64 kernel: ncu on 256 x 8192,
-# the bench lattice's height (37 DFMA + 29 integer-to-FP64 conversions + the
-# wall rows' FP64 sums, run by whole warps: 0.7 per site here, 5.6 at Ly = 1024)
-FP64_PIPE_INST_PER_SITE = 66.7
+# FP64-pipe instructions per site of the fused FP64 sites kernel (ncu on
+# 2048 x 1024: 37 DFMA + 29 integer-to-FP64 conversions; the wall rows' FP64
+# sums run in the wall-band kernel, 6 of the bench lattice's 8192 rows)
+FP64_PIPE_INST_PER_SITE = 66.0
 # FP64 pipe peak from unit counts and clocks: 2 FP64 instructions per SM per
 # clock (ncu: ...dfma_pred_on.avg.peak_sustained = 2) x 152 SMs x 2.07 GHz
 FP64_PEAK_GINST = 2 * 152 * 2.07
