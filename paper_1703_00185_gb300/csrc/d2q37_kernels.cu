@@ -41,10 +41,12 @@ constexpr int kWallBlock = 128;
 #ifndef D2Q37_SITE_MIN_BLOCKS
 #define D2Q37_SITE_MIN_BLOCKS 2
 #endif
-// The batched kernel reads its parameters from memory instead of the
-// constant bank and needs more registers than 128 (it spills 228 bytes per
-// thread there), but on GB300 it still ran the 64-lattice batch faster with
-// 4 blocks of 128 threads per SM (3150 MLUPS) than with 3 and no spills (2970).
+// The batched kernel (D2Q37_BATCH_MIN_BLOCKS x 128 threads per SM, whatever
+// its block_y) reads its parameters from memory instead of the constant bank
+// and spills a little at 128 registers (20 bytes per thread); with 3 blocks of
+// 128 and no spills it was slower (2970 MLUPS against 3150 for 4, an earlier
+// form of the kernel).  The batch's per-lattice shape (block_y = 0), which
+// runs the single-lattice kernels, is faster still on the 64-lattice workload.
 #ifndef D2Q37_BATCH_MIN_BLOCKS
 #define D2Q37_BATCH_MIN_BLOCKS 4
 #endif
