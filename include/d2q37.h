@@ -139,7 +139,11 @@ int lbm_fields_device(lbm_t* h, double* rho, double* u, double* T);
  * asynchronous CUDA error as LBM_ECUDA. */
 int lbm_synchronize(lbm_t* h);
 
-/* Number of CUDA kernel launches this handle has enqueued so far. */
+/* Number of CUDA kernels this handle has enqueued so far, graph replays
+ * included: a fused FP64 step of a lattice with walls is two (the sites, then
+ * the wall-band rows), a fused FP32-storage step or one without walls one; a
+ * separate step one per phase run (propagate, bc with walls, collide); pbc
+ * one. */
 int64_t lbm_launch_count(const lbm_t* h);
 
 /* Kernel kinds reported by lbm_kernel_times(). */
