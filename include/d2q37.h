@@ -247,11 +247,12 @@ int lbm_batch_step_static(int n, lbm_t* const* lattices, int steps, void* cuda_s
  * pass ones that do not fit yet, whenever their device memory
  * (lbm_required_bytes) fits in the free part of one pre-allocated pool of
  * hbm_budget_bytes.  Each lbm_server_tick admits what fits, advances every
- * admitted job by k = min(max_steps_per_tick, fewest steps left) steps with
- * its fused kernel, once per step on the job's stream (one of four, assigned
- * at admission to the one with the fewest active sites, so that the jobs run
- * side by side), then copies the fields of jobs that reached their step
- * count to host memory and frees their device memory.
+ * admitted job by k = min(max_steps_per_tick, fewest steps left) steps of
+ * its fused step (as lbm_step: replays of a captured two-step graph) on the
+ * job's stream (one of four, assigned at admission to the one with the fewest
+ * active sites, so that the jobs run side by side), then copies the fields of
+ * jobs that reached their step count to host memory and frees their device
+ * memory.
  * All calls are from one host thread; a tick synchronises its streams. */
 typedef struct lbm_server_t lbm_server_t;
 

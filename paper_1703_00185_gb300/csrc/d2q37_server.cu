@@ -6,11 +6,11 @@
 // that fits, whenever their device memory fits in the free part of one
 // pre-allocated pool (the HBM budget; first-fit with coalescing).  Admitted
 // jobs keep their state on the device.  Each tick advances every active job
-// by k steps, k = min(steps per tick, fewest steps left), with the fused
-// kernel of its precision once per step on the job's stream: one of kStreams
-// streams, assigned at admission to the one with the fewest active sites, so
-// that the jobs' launches run side by side (on GB300 this beat one batched
-// launch per step over all jobs by 14-30 %).  A job that reaches its step count has its
+// by k steps, k = min(steps per tick, fewest steps left), through its own
+// handle's step (replays of captured two-step graphs of the fused step) on
+// the job's stream: one of kStreams streams, assigned at admission to the one
+// with the fewest active sites, so that the jobs run side by side (on GB300
+// per-job launches beat one batched launch per step over all jobs by 14-30 %).  A job that reaches its step count has its
 // fields copied to host memory and its device memory returned to the pool;
 // the next tick can admit queued jobs into it.
 #include <algorithm>
@@ -209,25 +209,18 @@ int lbm_server_tick(lbm_server_t* s, int* steps_done) {
   if (s->active.empty()) return LBM_OK;
   int k = s->max_steps_per_tick;
   for (Job* j : s->active) k = std::min(k, j->steps_left);
-  // each job's k steps in order on its stream; the streams run side by side
+  // each job's k steps in order on its stream (lbm_step: replays of its
+  // captured two-step graphs, one host launch per two steps); the streams run
+  // side by side
   for (Job* j : s->active) {
-    lbm_t* h = j->h;
-    cudaStream_t st = s->stream[j->stream];
-    for (int t = 0; t < k; ++t) {
-      const int c = h->cur ^ (t & 1);
-      const int launched =
-          j->prm.precision == LBM_PRECISION_FP64
-              ? launch_fused((const double*)h->buf[c], (double*)h->buf[c ^ 1], h->sp, st)
-              : launch_fused32((const float*)h->buf[c], (float*)h->buf[c ^ 1], h->sp,
-                               j->prm.precision == LBM_PRECISION_FP32_FP64, st);
-      if (launched < 0) return LBM_ECUDA;
-      s->stats.launches += launched;
-    }
+    const int64_t before = j->h->launches;
+    rc = lbm_step(j->h, k);
+    if (rc) return rc;
+    s->stats.launches += j->h->launches - before;
   }
   // completed jobs: fields into their scratch, then to host
   std::vector<Job*> done;
   for (Job* j : s->active) {
-    j->h->cur ^= (k & 1);
     j->steps_left -= k;
     if (j->steps_left == 0) done.push_back(j);
   }
