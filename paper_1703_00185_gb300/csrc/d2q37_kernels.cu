@@ -731,6 +731,10 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(c
                                                         StepParams p) {
   const int x = blockIdx.x;
   const int y = blockIdx.y * kBlockY + threadIdx.x;
+  // the wall-band kernel, launched next with programmatic stream
+  // serialization, reads and writes nothing this kernel writes: it may start
+  // once every block of this one has started, and fill the tail
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (y >= p.Ly) return;
   if (!p.periodic_y && (y < 3 || y >= p.Ly - 3)) return;  // wall_band_kernel's
   fused_site<true, false>(src, dst, p, p, x, y);
@@ -854,7 +858,16 @@ int launch_collide(double* buf, const StepParams& p, cudaStream_t stream) {
 int launch_fused(const double* src, double* dst, const StepParams& p, cudaStream_t stream) {
   fused_kernel<<<site_grid(p), kBlockY, 0, stream>>>(src, dst, p);
   if (p.periodic_y) return done(1);
-  wall_band_kernel<<<(6 * p.Lx + kWallBlock - 1) / kWallBlock, kWallBlock, 0, stream>>>(src, dst, p);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((6 * p.Lx + kWallBlock - 1) / kWallBlock);
+  cfg.blockDim = dim3(kWallBlock);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, wall_band_kernel, src, dst, p) != cudaSuccess) return -1;
   return done(2);
 }
 
