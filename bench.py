@@ -44,8 +44,8 @@ FP64_PEAK_GINST = 2 * 152 * 2.07
 ORACLE_FLOPS_PER_SITE = 42640
 ORACLE_NONTRIVIAL_FLOPS_PER_SITE = 17477
 # DRAM bytes per fused launch at 2048 x 8192, scaled by sites from the ncu
-# capture of the same kernel on 2048 x 1024 (1222.7 MB per launch there)
-FUSED_TRAFFIC_BYTES_2048x8192 = 1222.7e6 * 8
+# capture of the same kernel on 2048 x 1024 (1223.0 MB per launch there)
+FUSED_TRAFFIC_BYTES_2048x8192 = 1223.0e6 * 8
 # the same for the FP32-storage double-float kernel, from its capture on
 # 2048 x 2048 (1273.0 MB per launch there)
 FUSED32_DF_TRAFFIC_BYTES_2048x8192 = 1273.0e6 * 4
