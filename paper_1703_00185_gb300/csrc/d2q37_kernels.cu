@@ -195,8 +195,9 @@ __device__ __forceinline__ double hop_dot(int cx, int cy, const double (&mx)[3],
 // product and keeps 2^-55 or better absolute precision on the order-1
 // quantities; exact integer sums remove the cancellation that
 // limits the FP64 form near T = 0.5 for the outer shells.  Per population
-// the result is turned into an FP64 number with integer operations and
-// relaxed with one FP64 FMA.  The shell factor omega w_k is carried as
+// the result is turned into an FP64 number (fx_to_double: the FP64 pipe's
+// integer conversion, or integer operations for the shells of
+// D2Q37_INT_CVT_MASK) and relaxed with one FP64 FMA.  The shell factor omega w_k is carried as
 // c_k 2^E_k with c_k in [0.5, 1).  The ranges that keep every intermediate
 // inside its format hold for rho in (0, 4), |T_bar - 1| < 1 and |u_bar| < 0.35
 // per component; other sites take the FP64 evaluation.
@@ -206,7 +207,7 @@ __device__ __forceinline__ double hop_dot(int cx, int cy, const double (&mx)[3],
 // M0 = rho (B2 - 3 theta / 2), M1 = rho theta / 4 (site values), the shell
 // coefficients of collide_site times c_k rho are
 //   R0 = c (K0 + x2 K1 + x2^2 K2),  R1 = c (L0 + x2 L1),  R2 = c (M0 + x2 M1),
-//   R3 = c rho / 6,  R4 = c rho / 24,
+//   R3 = c rho / 6,  R4 = c rho / 24 (one product: (c/6) 2^64 is (c/24) 2^66),
 // and per pair even = R0 + b (R2 + b R4), odd = a (R1 + b R3), b = a^2.
 // A signed site value x meets the unsigned shell constants as x + 2^63 (its
 // sign bit flipped), which needs no sign fix: x y 2^-64 = (x + 2^63) y 2^-64
