@@ -250,8 +250,8 @@ def roofline_of(kind, avg_s, sites, precision, traffic=None):
          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
          "algorithmic_bytes_per_launch": nbytes}
     if precision == "fp64" and kind in ("fused", "collide"):
-        # the roofline of the survey's formula, min(HBM / bytes, FP64 peak / flops),
-        # with the oracle's flop count: this step does not spend those flops
+        # the roofline min(HBM / bytes, FP64 peak / flops) with the oracle's flop
+        # count: this step does not spend those flops
         # (integer moments, fixed-point equilibrium), so the HBM one binds
         peak_flops = 2 * FP64_PEAK_GINST * 1e9
         r["oracle_flops"] = {"flops_per_site": ORACLE_FLOPS_PER_SITE,
