@@ -2,13 +2,18 @@
 
 The CUDA collision evaluates the equilibrium, and the site values it needs,
 in 64-bit integers with a power-of-two scale per quantity, every product
-being the high word of a 64 x 64-bit product.  This module restates those
-integer operations in Python (exact integers, the same scales and the same
-order) and checks them against exact rational arithmetic: no intermediate
-leaves its 64-bit format anywhere inside the fixed-point ranges
-(rho in (0, 4), |u| < 0.35 per component, |T_bar - 1| < 1), and the results
-are better than FP64 rounding.  It is a check of the formats, not of the
-kernel: the kernel itself is held to the oracle by the GPU tests.
+being the high word of a 64 x 64-bit product: exact (floor), with the
+low-by-low partial product left out (the per-pair products), or rounded (the
+odd part); signed site values meet the shell constants shifted by 2^63, with
+the offsets and rounding corrections in per-shell constants, and the
+conversion sets the result's lowest bit.  This module restates those integer
+operations in Python (exact integers, the same scales and the same order)
+and checks them against exact rational arithmetic: no intermediate leaves its
+64-bit format anywhere inside the fixed-point ranges (rho in (0, 4),
+|u| < 0.35 per component, |T_bar - 1| < 1), and the results are better than
+FP64 rounding.  It also recomputes the moment sums' floor compensation.  It is
+a check of the formats, not of the kernel: the kernel itself is held to the
+oracle by the GPU tests.
 """
 import math
 import os
