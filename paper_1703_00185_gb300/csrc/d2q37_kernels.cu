@@ -270,25 +270,6 @@ __device__ __forceinline__ long long mul_shift(long long x, long long y, int sh)
   return (long long)((h << (64 - sh)) | (l >> sh));
 }
 
-// round(v 2^Q) for |v| 2^Q < 2^63 (zero and subnormal inputs give 0)
-template <int Q>
-__device__ __forceinline__ long long to_fx(double v) {
-  const int hi = __double2hiint(v);
-  const unsigned lo = (unsigned)__double2loint(v);
-  const int e = (hi >> 20) & 0x7FF;
-  const long long m = ((long long)((hi & 0xFFFFF) | 0x100000) << 32) | lo;
-  const int sh = e - (1075 - Q);  // v 2^Q = m 2^sh, sh <= 10 below 2^63
-  long long r;
-  if (sh >= 0) {
-    r = m << sh;
-  } else {
-    const int rs = min(-sh, 63);
-    r = (m + (1LL << (rs - 1))) >> rs;
-  }
-  r = e ? r : 0;
-  return hi < 0 ? -r : r;
-}
-
 // g 2^(E - 55) as an FP64 number, two ways: with the FP64 pipe's 64-bit
 // integer conversion (round to nearest even) and the power of two added to
 // the exponent field, or with integer operations only (round half away from
