@@ -47,8 +47,6 @@ __device__ __forceinline__ dfloat df_add(dfloat x, dfloat y) {
   return df_fast_two_sum(s.hi, s.lo);
 }
 
-__device__ __forceinline__ dfloat df_sub(dfloat x, dfloat y) { return df_add(x, df_neg(y)); }
-
 // "Sloppy" addition (one two-sum instead of two): relative error about
 // 2^-44 even when the low parts cancel, 11 FP32 operations instead of 20.
 __device__ __forceinline__ dfloat df_add_fast(dfloat x, dfloat y) {
@@ -74,9 +72,6 @@ __device__ __forceinline__ dfloat df_mul(dfloat x, float y) {
   p.lo = __fmaf_rn(x.lo, y, p.lo);
   return df_fast_two_sum(p.hi, p.lo);
 }
-
-// x * y + z
-__device__ __forceinline__ dfloat df_fma(dfloat x, dfloat y, dfloat z) { return df_add(df_mul(x, y), z); }
 
 // K0 + x (K1 + x K2) (Horner) with sloppy additions.
 __device__ __forceinline__ dfloat df_quad(dfloat K0, dfloat K1, dfloat K2, dfloat x) {
