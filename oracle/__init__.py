@@ -54,8 +54,9 @@ _FLOP_LIB = os.path.join(_LIB_DIR, "liboracle_d2q37_flops.so")
 
 def build_flop_counter(force=False):
     """Compile the counting build (g++); returns the library path."""
+    srcs = (_FLOP_SRC, _SRC, os.path.join(_HERE, "collide_contracted.c"))
     if force or not os.path.exists(_FLOP_LIB) or \
-            os.path.getmtime(_FLOP_LIB) < max(os.path.getmtime(_FLOP_SRC), os.path.getmtime(_SRC)):
+            os.path.getmtime(_FLOP_LIB) < max(os.path.getmtime(p) for p in srcs):
         os.makedirs(_LIB_DIR, exist_ok=True)
         tmp = _FLOP_LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fpermissive",
@@ -81,6 +82,39 @@ def collide_flops_per_site(nontrivial=False):
     w_shell = np.ascontiguousarray([float(np.asarray(w)[c2.index(k)]) for k in sorted(set(c2))])
     lib.orc_count_setup(float(s), w_shell.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return int(lib.orc_count_collide_site(1 if nontrivial else 0))
+
+
+def _flop_lib():
+    lib = ctypes.CDLL(build_flop_counter())
+    lib.orc_count_setup.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.orc_count_setup.restype = ctypes.c_int
+    lib.orc_count_collide_form.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.orc_count_collide_form.restype = ctypes.c_longlong
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.orc_collide_form_values.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+    s, w = scale_and_weights()
+    cx, cy = velocity_set()
+    c2 = (np.asarray(cx) ** 2 + np.asarray(cy) ** 2).tolist()
+    w_shell = np.ascontiguousarray([float(np.asarray(w)[c2.index(k)]) for k in sorted(set(c2))])
+    lib.orc_count_setup(float(s), w_shell.ctypes.data_as(dp))
+    return lib
+
+
+def contracted_collide_flops_per_site(nontrivial=False):
+    """FP64 operations of one site collision with the equilibrium contracted
+    by hand into its scalar polynomial (oracle/collide_contracted.c), every
+    population evaluated on its own: the plain per-site FP64 work of the
+    method, counted by the same counting build."""
+    return int(_flop_lib().orc_count_collide_form(1, 1 if nontrivial else 0))
+
+
+def counted_collide_values(f, tau, gx, gy, contracted):
+    """The relaxed populations of one site from the counting build, in the
+    oracle's tensor form (contracted=False) or the hand-contracted one."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(Q)
+    _flop_lib().orc_collide_form_values(1 if contracted else 0, _p(f), tau, gx, gy, _p(out))
+    return out
 
 
 def _load():

@@ -4,10 +4,12 @@
  * The oracle's C source is compiled here as C++ with its `double` replaced by
  * a type that counts every floating-point addition, subtraction,
  * multiplication and division it performs (comparisons, conversions and
- * copies are not counted).  The arithmetic itself is unchanged.  The one
- * export, orc_count_collide_site, returns the operations of one site
- * collision (moments, shifted fields, equilibrium, relaxation), the FP64
- * flop count of the method as the oracle writes it out.
+ * copies are not counted).  The arithmetic itself is unchanged.
+ * orc_count_collide_form returns the operations of one site collision
+ * (moments, shifted fields, equilibrium, relaxation), in the oracle's form
+ * (the equilibrium as the full Hermite tensor contractions) or in the
+ * hand-contracted scalar form of collide_contracted.c, the plain
+ * per-population FP64 work of the method.
  */
 #include <math.h>
 #include <stdint.h>
@@ -58,22 +60,40 @@ inline cd operator/(cd a, int b) { return a / cd((double)b); }
 using flopcount::cd;
 #define double cd
 #include "d2q37_oracle.c"
+#include "collide_contracted.c"
 #undef double
 
 extern "C" {
 
 /* FP64 operations of one site collision of the oracle (orc_count_setup
- * first): all of them, or (nontrivial != 0) those without a trivial operand. */
-long long orc_count_collide_site(int nontrivial) {
-  double f[Q], out[Q];
-  for (int l = 0; l < Q; ++l) f[l] = (double)w_[l].v * (1.0 + 0.01 * (l % 5));
+ * first): all of them, or (nontrivial != 0) those without a trivial operand.
+ * form 0: the oracle's collision (equilibrium as the full tensor
+ * contractions); form 1: the same collision with the hand-contracted scalar
+ * equilibrium of collide_contracted.c. */
+long long orc_count_collide_form(int form, int nontrivial) {
+  cd fc[Q], oc[Q];
+  for (int l = 0; l < Q; ++l) fc[l] = cd(w_[l].v * (1.0 + 0.01 * (l % 5)));
+  flopcount::g_ops = flopcount::g_nontrivial = 0;
+  if (form == 0)
+    orc_collide_site(fc, cd(0.8), cd(0.0), cd(-1e-4), oc);
+  else
+    orc_collide_site_contracted(fc, cd(0.8), cd(0.0), cd(-1e-4), oc);
+  return (long long)(nontrivial ? flopcount::g_nontrivial : flopcount::g_ops);
+}
+
+long long orc_count_collide_site(int nontrivial) { return orc_count_collide_form(0, nontrivial); }
+
+/* The relaxed populations of either form for populations f (plain doubles
+ * in and out), so that tests can check that the counted forms agree. */
+void orc_collide_form_values(int form, const double* f, double tau, double gx, double gy,
+                             double* out) {
   cd fc[Q], oc[Q];
   for (int l = 0; l < Q; ++l) fc[l] = cd(f[l]);
-  flopcount::g_ops = flopcount::g_nontrivial = 0;
-  orc_collide_site(fc, cd(0.8), cd(0.0), cd(-1e-4), oc);
+  if (form == 0)
+    orc_collide_site(fc, cd(tau), cd(gx), cd(gy), oc);
+  else
+    orc_collide_site_contracted(fc, cd(tau), cd(gx), cd(gy), oc);
   for (int l = 0; l < Q; ++l) out[l] = oc[l].v;
-  (void)out;
-  return (long long)(nontrivial ? flopcount::g_nontrivial : flopcount::g_ops);
 }
 
 }

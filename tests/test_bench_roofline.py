@@ -29,7 +29,15 @@ def test_fp64_fused_entry(peaks):
     assert fp["inst_per_site"] == bench.FP64_PIPE_INST_PER_SITE
     assert fp["achieved"] == pytest.approx(bench.FP64_PIPE_INST_PER_SITE * sites / step_s / 1e9, abs=0.01)
     assert fp["peak"] == pytest.approx(2 * 152 * 2.07, abs=0.01)
-    assert r["oracle_flops"]["flops_per_site"] == bench.ORACLE_FLOPS_PER_SITE
+    assert r["oracle_flops"]["tensor_form_flops_per_site"] == bench.ORACLE_FLOPS_PER_SITE
+    assert r["oracle_flops"]["contracted_flops_per_site"] == bench.ORACLE_CONTRACTED_FLOPS_PER_SITE
+    # both terms of min(HBM / bytes, FP64 peak / flops)
+    b = r["bounds"]
+    assert b["hbm_gsites_per_s"] == pytest.approx(6775.3 / 592, abs=1e-3)
+    flop = 2 * 2 * 152 * 2.07e9 / bench.ORACLE_CONTRACTED_FLOPS_PER_SITE / 1e9
+    assert b["fp64_flop_gsites_per_s"] == pytest.approx(flop, abs=1e-4)
+    assert b["min_gsites_per_s"] == pytest.approx(min(6775.3 / 592, flop), abs=1e-4)
+    assert b["achieved_gsites_per_s"] == pytest.approx(sites / step_s / 1e9, abs=1e-4)
 
 
 def test_fp32_entry_has_no_fp64_sides(peaks):
