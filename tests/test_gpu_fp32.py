@@ -89,7 +89,7 @@ def oracle_1000():
     return {100: f100, 1000: o.fields()}
 
 
-# Bars: measured errors times ~3 (the design doc lists the measured values).
+# Bars: measured errors times ~3.
 ACC_BARS = {100: (2e-7, 5e-5, 2e-7), 1000: (1e-6, 1e-4, 1e-6)}
 
 
