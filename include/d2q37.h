@@ -58,6 +58,9 @@ extern "C" {
 /* Kernel schedules for lbm_params.kernel. */
 #define LBM_KERNEL_SEPARATE 0 /* pbc, propagate, bc, collide as separate kernels */
 #define LBM_KERNEL_FUSED 1    /* pbc, then one fused propagate+bc+collide kernel */
+#define LBM_KERNEL_FUSED_SERIAL 2 /* as FUSED; the FP64 wall-band kernel starts only after the sites
+                                     kernel has finished (FUSED lets it start in that kernel's tail);
+                                     the results are the same bit for bit */
 
 typedef struct lbm_t lbm_t;
 
@@ -70,7 +73,7 @@ typedef struct {
                      d_l = f_l - w_l from the lattice weights (half the memory traffic) with the
                      moment sums exact in 64-bit integers and rho, u, T and the temperature-
                      dependent equilibrium terms in FP64 or in double-float */
-  int kernel;     /* LBM_KERNEL_SEPARATE or LBM_KERNEL_FUSED */
+  int kernel;     /* LBM_KERNEL_SEPARATE, LBM_KERNEL_FUSED or LBM_KERNEL_FUSED_SERIAL */
   int periodic_y; /* 1: no walls, y periodic too (used by tests of pure propagation) */
 } lbm_params;
 
@@ -236,7 +239,14 @@ void lbm_batch_destroy(lbm_batch_t* b);
  *    the GPU race on it, so order them (one stream, or events).
  *  - The caller orders the lattices' own pending work before this call; the
  *    lattices' current buffers are updated on return (work still in flight
- *    on cuda_stream). */
+ *    on cuda_stream).
+ *  - The table reaches the device by a copy from pageable host memory, so
+ *    each call waits on the host for the work already queued on cuda_stream.
+ *  - Every lattice's memory must be on the current device (LBM_EINVAL
+ *    otherwise), and cuda_stream must not be capturing (LBM_EINVAL): the
+ *    current buffers are switched on the host at call time.
+ *  - The batched launches are counted by no handle's lbm_launch_count (as
+ *    lbm_batch_step's are counted on its batch, not on its lattices). */
 #define LBM_STATIC_BATCH_MAX 256
 int lbm_batch_step_static(int n, lbm_t* const* lattices, int steps, void* cuda_stream);
 

@@ -17,7 +17,7 @@ Q = 37
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ESTATE, LBM_ETOOBIG = 0, -1, -2, -3, -4, -5, -6
 LBM_STATIC_BATCH_MAX = 256
 PHASE_PROPAGATE, PHASE_BC, PHASE_COLLIDE, PHASE_ALL = 1, 2, 4, 7
-KERNEL_SEPARATE, KERNEL_FUSED = 0, 1
+KERNEL_SEPARATE, KERNEL_FUSED, KERNEL_FUSED_SERIAL = 0, 1, 2
 PRECISION_FP64, PRECISION_FP32_FP64, PRECISION_FP32_DF = 0, 1, 2
 PRECISIONS = {"fp64": PRECISION_FP64, "fp32": PRECISION_FP32_FP64, "fp32-df": PRECISION_FP32_DF}
 
@@ -241,8 +241,10 @@ def lbm_batch_step_static(handles, steps, cuda_stream):
 class Lattice:
     """One Lx x Ly lattice on a CUDA device, memory owned by PyTorch.
 
-    ``kernel`` is "fused" (one propagate/bc/collide kernel per step) or
-    "separate" (propagate, bc, collide).  ``precision`` is "fp64", "fp32"
+    ``kernel`` is "fused" (one propagate/bc/collide pass per step: the sites
+    kernel and, with walls, the wall-band kernel started in its tail),
+    "fused_serial" (the same two kernels one after the other) or "separate"
+    (propagate, bc, collide).  ``precision`` is "fp64", "fp32"
     (FP32 deviation storage, FP64 wide terms) or "fp32-df" (FP32 deviation
     storage, double-float wide terms).  All work runs on ``stream`` (default:
     the current PyTorch stream of ``device``)."""
@@ -258,7 +260,7 @@ class Lattice:
             self.device = torch.device("cuda", torch.cuda.current_device())
         p = lbm_default_params()
         p.tau, p.g0, p.T_top, p.T_bot = tau, g0, T_top, T_bot
-        p.kernel = {"fused": KERNEL_FUSED, "separate": KERNEL_SEPARATE}[kernel]
+        p.kernel = {"fused": KERNEL_FUSED, "separate": KERNEL_SEPARATE, "fused_serial": KERNEL_FUSED_SERIAL}[kernel]
         p.precision = PRECISIONS[precision]
         self.precision = precision
         p.periodic_y = int(bool(periodic_y))

@@ -147,7 +147,8 @@ bool valid_params(int Lx, int Ly, const lbm_params* p) {
   if (p->precision != LBM_PRECISION_FP64 && p->precision != LBM_PRECISION_FP32_FP64 &&
       p->precision != LBM_PRECISION_FP32_DF)
     return false;
-  if (p->kernel != LBM_KERNEL_SEPARATE && p->kernel != LBM_KERNEL_FUSED) return false;
+  if (p->kernel != LBM_KERNEL_SEPARATE && p->kernel != LBM_KERNEL_FUSED && p->kernel != LBM_KERNEL_FUSED_SERIAL)
+    return false;
   if ((long long)Lx * Ly > (1LL << 34)) return false;
   // one population plane must stay below 2^31 elements (32-bit in-plane offsets)
   if ((long long)(Lx + 2 * kHx) * frame_ny(Ly, p->precision) >= (1LL << 31)) return false;
@@ -282,7 +283,7 @@ int k_collide(lbm_t* h, void* b) {
 int k_fused(lbm_t* h, const void* s, void* d) {
   return is_fp32(h->prec)
              ? launch_fused32((const float*)s, (float*)d, h->sp, h->prec == LBM_PRECISION_FP32_FP64, h->stream)
-             : launch_fused((const double*)s, (double*)d, h->sp, h->stream);
+             : launch_fused((const double*)s, (double*)d, h->sp, h->stream, h->prm.kernel != LBM_KERNEL_FUSED_SERIAL);
 }
 
 int k_fields(lbm_t* h, const void* b, double* rho, double* u, double* T) {
@@ -579,7 +580,7 @@ int lbm_get_populations(lbm_t* h, double* f) {
 int lbm_step(lbm_t* h, int n) {
   if (!h || n < 0) return LBM_EINVAL;
   if (!h->have_state) return LBM_ESTATE;
-  const bool fused = h->prm.kernel == LBM_KERNEL_FUSED;
+  const bool fused = h->prm.kernel != LBM_KERNEL_SEPARATE;
   int t = 0;
   if (fused && !h->timing && n >= 4) {
     if (!h->halo_valid) {

@@ -58,6 +58,26 @@ int lbm_batch_step_static(int n, lbm_t* const* lattices, int steps, void* cuda_s
   }
   if (steps == 0) return LBM_OK;
   const cudaStream_t stream = (cudaStream_t)cuda_stream;
+  // The lattices' current buffers are switched here, on the host, and the
+  // table is copied from host memory that the next call rewrites: work
+  // recorded into a graph would replay with stale buffers and table.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_ECUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return LBM_EINVAL;
+  // every lattice's memory must be on the current device, where the table is
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
+  for (int i = 0; i < n; ++i) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, lattices[i]->buf[0]) != cudaSuccess) {
+      cudaGetLastError();
+      return LBM_EINVAL;
+    }
+    if (a.type != cudaMemoryTypeDevice || a.device != dev) return LBM_EINVAL;
+  }
   std::lock_guard<std::mutex> lock(g_static_mutex);
   int rc = handle_device_consts();
   BatchEntry* dev_tab = nullptr;
@@ -77,7 +97,8 @@ int lbm_batch_step_static(int n, lbm_t* const* lattices, int steps, void* cuda_s
     e.tile0 = tiles;
     tiles += (long long)lattices[i]->Lx * e.ytiles;
   }
-  // pageable source: the copy has consumed g_static_host when this returns
+  // pageable source: the runtime stages it before the call returns (so the
+  // next call may rewrite it), which waits for the stream's earlier work
   if (cudaMemcpyAsync(dev_tab, g_static_host, n * sizeof(BatchEntry), cudaMemcpyHostToDevice, stream) !=
       cudaSuccess)
     return LBM_ECUDA;

@@ -726,12 +726,22 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(c
 // Ly - 3..Ly - 1, walls only): packed 32 sites to a warp, so that the wall
 // bc's work runs in full warps instead of in three lanes of a fused_kernel
 // warp (a warp holding wall rows cost about three ordinary warps there).
+// When it is launched as a programmatic dependent of fused_kernel it may run
+// while that kernel's last blocks still run; every thread then waits for the
+// sites kernel to complete (griddepcontrol.wait: the prerequisite grid has
+// finished and its writes are visible) before it exits.  So this grid never
+// completes before the sites kernel, and whatever the stream runs after it
+// (the next step's sites kernel reads both kernels' rows) is ordered after
+// both, in a stream and in a captured graph alike.  Launched normally, the
+// wait returns at once.
 __global__ void __launch_bounds__(kWallBlock) wall_band_kernel(const double* __restrict__ src,
                                                               double* __restrict__ dst, StepParams p) {
   const int t = blockIdx.x * kWallBlock + threadIdx.x;
-  if (t >= 6 * p.Lx) return;
-  const int x = t / 6, k = t - 6 * x;
-  fused_site<true, true>(src, dst, p, p, x, k < 3 ? k : p.Ly - 6 + k);
+  if (t < 6 * p.Lx) {
+    const int x = t / 6, k = t - 6 * x;
+    fused_site<true, true>(src, dst, p, p, x, k < 3 ? k : p.Ly - 6 + k);
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Many lattices in one launch: block-sized tiles (one column x, BY
@@ -837,9 +847,13 @@ int launch_collide(double* buf, const StepParams& p, cudaStream_t stream) {
   return done(1);
 }
 
-int launch_fused(const double* src, double* dst, const StepParams& p, cudaStream_t stream) {
+int launch_fused(const double* src, double* dst, const StepParams& p, cudaStream_t stream, bool overlap) {
   fused_kernel<<<site_grid(p), kBlockY, 0, stream>>>(src, dst, p);
   if (p.periodic_y) return done(1);
+  if (!overlap) {
+    wall_band_kernel<<<(6 * p.Lx + kWallBlock - 1) / kWallBlock, kWallBlock, 0, stream>>>(src, dst, p);
+    return done(2);
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((6 * p.Lx + kWallBlock - 1) / kWallBlock);
   cfg.blockDim = dim3(kWallBlock);

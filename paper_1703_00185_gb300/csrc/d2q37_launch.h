@@ -16,7 +16,9 @@ int launch_wrap(double* buf, const StepParams& p, cudaStream_t stream);
 int launch_propagate(const double* src, double* dst, const StepParams& p, cudaStream_t stream);
 int launch_bc(const double* src, double* dst, const StepParams& p, cudaStream_t stream);
 int launch_collide(double* buf, const StepParams& p, cudaStream_t stream);
-int launch_fused(const double* src, double* dst, const StepParams& p, cudaStream_t stream);
+// overlap: the wall-band kernel (walls only) is launched as a programmatic
+// dependent of the sites kernel and starts in its tail; false: after it.
+int launch_fused(const double* src, double* dst, const StepParams& p, cudaStream_t stream, bool overlap = true);
 int launch_fields(const double* buf, double* rho, double* u, double* T, const StepParams& p, cudaStream_t stream);
 int launch_init_equilibrium(double* buf, const double* T, const StepParams& p, cudaStream_t stream);
 

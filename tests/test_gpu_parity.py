@@ -231,11 +231,59 @@ def test_errors_and_edge_cases():
     lbm.lbm_destroy(h)
 
 
+def test_overlapped_wall_band_matches_serial():
+    """The fused FP64 step launches its wall-band kernel as a programmatic
+    dependent of the sites kernel, so that it starts in that kernel's tail.
+    20 steps of the 2048 x 8192 bench lattice that way (replayed from the
+    captured two-step graph, as bench.py runs them) are bit-identical to the
+    same steps with the two kernels one after the other."""
+    import torch
+    Lx, Ly = 2048, 8192
+    out = []
+    for kernel in ("fused", "fused_serial"):
+        g = lbm.Lattice(Lx, Ly, kernel=kernel, device="cuda:0", stream=torch.cuda.Stream(device="cuda:0"))
+        g.init_rayleigh_taylor(1)
+        g.step(20)
+        out.append(g.populations())
+        g.close()
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("T_bot,T_top", [(1.5, 0.5), (0.8, 1.2)])
+def test_walls_steady_conduction(T_bot, T_top, perm):
+    """Steady heat conduction between the walls (g = 0, 3000 steps): the
+    library against the oracle, whose profile the CPU tests pin to each wall's
+    own temperature."""
+    kw = dict(tau=0.8, g0=0.0, T_top=T_top, T_bot=T_bot)
+    g, o = pair(3, 24, kernel="fused", **kw)
+    o.set_equilibrium(1.0, 0.0, 0.0, 0.5 * (T_bot + T_top))
+    g.set_populations(o.populations()[perm])
+    n = oracle.threads()
+    oracle.set_threads(1)
+    try:
+        o.run(3000)
+    finally:
+        oracle.set_threads(n)
+    g.step(3000)
+    (rho, u, T), (orho, ou, oT) = g.fields(), o.fields()
+    assert max(rel_field_errors((rho, T), (orho, oT))) <= FIELD_TOL
+    # u: the steady state holds only a weak flow in the wall layers (|u| < 1e-3),
+    # so u is compared in the unit of velocity (the thermal speed at T = 1)
+    # rather than relative to its own small maximum
+    assert np.abs(u - ou).max() <= FIELD_TOL
+
+
 def test_full_size_sampled_columns(perm):
     """2048 x 8192 in the fused schedule bench.py times: 2 steps from the
     Rayleigh-Taylor state, sampled columns recomputed by the oracle on 13-column
     windows (after 2 steps a column depends on its +-6 neighbours only), plus
-    global mass conservation."""
+    global mass conservation.
+
+    Bar per population plane: (steps + 1) POP_TOL.  The two sides' initial
+    equilibria differ by ~2e-15 of a plane's largest value (measured 1.6e-15 to
+    1.8e-15), and every step's collision adds at most about POP_TOL, the
+    one-collision bar (measured on these columns: 0.9e-14 to 1.1e-14 after one
+    step, 1.1e-14 to 1.5e-14 after two)."""
     Lx, Ly, seed, steps = 2048, 8192, 1, 2
     g = lbm.Lattice(Lx, Ly, kernel="fused", device="cuda:0")
     g.init_rayleigh_taylor(seed)
@@ -254,5 +302,4 @@ def test_full_size_sampled_columns(perm):
         o.run(steps)
         ref = o.populations()[perm][:, 6]
         got = f[:, x]
-        # initial equilibrium + 2 steps, each side rounding differently: 10x the one-phase bar
-        assert plane_rel_err(got, ref) <= 10 * POP_TOL, x
+        assert plane_rel_err(got, ref) <= (steps + 1) * POP_TOL, x

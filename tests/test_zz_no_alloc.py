@@ -2,8 +2,9 @@
 call cudaMalloc (device memory owned by a caching allocator or a registered
 pool, loops that must not synchronise the device).  Through the C ABI, two
 calls in a row must give the same populations as the allocating batched entry
-point (lbm_batch_*), bit for bit as the other batched tests require; and a
-call with more lattices than the fixed table holds must be refused.
+point (lbm_batch_*), bit for bit as the other batched tests require, while the
+device's free memory stays the same; a call with more lattices than the fixed
+table holds, and a call on a stream that is capturing, must be refused.
 
 Kept in a file of its own, collected last."""
 import numpy as np
@@ -46,8 +47,11 @@ def test_static_batch_matches_allocating_batch(precision):
         batch.synchronize()
         for lat in stat:
             lat.synchronize()
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info(0)[0]
         lbm.lbm_batch_step_static([lat._h for lat in stat], steps, stream.cuda_stream)
         stream.synchronize()
+        assert torch.cuda.mem_get_info(0)[0] == free0  # nothing allocated on the device
         for a, b in zip(ref, stat):
             assert np.array_equal(a.populations(), b.populations())
     batch.close()
@@ -63,4 +67,20 @@ def test_static_batch_refuses_too_many_lattices():
         lbm.lbm_batch_step_static([lat._h] * (lbm.LBM_STATIC_BATCH_MAX + 1), 2, stream.cuda_stream)
     assert e.value.code == lbm.LBM_ETOOBIG
     assert "static table" in lbm.lbm_strerror(lbm.LBM_ETOOBIG)
+    assert np.array_equal(lat.populations(), before)
+
+
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
+def test_static_batch_refuses_a_capturing_stream():
+    import torch
+    lat = lbm.Lattice(16, 16, device="cuda:0")
+    lat.init_rayleigh_taylor(1)
+    lat.synchronize()
+    before = lat.populations()
+    stream = torch.cuda.Stream(device="cuda:0")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_batch_step_static([lat._h], 2, stream.cuda_stream)
+    assert e.value.code == lbm.LBM_EINVAL
     assert np.array_equal(lat.populations(), before)
