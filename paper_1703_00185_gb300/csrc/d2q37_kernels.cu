@@ -400,6 +400,13 @@ __device__ __forceinline__ bool fx_site_from_sums(long long r, long long jx, lon
   return true;
 }
 
+// Where the relaxation reads each population's pre-collision value (the
+// site's register array).
+struct PopRegs {
+  const double (&f)[kQ];
+  __device__ __forceinline__ double operator()(int l) const { return f[l]; }
+};
+
 // Where a collision puts the relaxed populations: straight into the site's
 // planes of the destination, so that each pair's registers are free once it
 // is relaxed.
@@ -416,9 +423,8 @@ struct ToPlanesStride {  // the same with the planes addressed as multiples of t
 
 // The collision of collide_site_fp64 below with the equilibrium in fixed
 // point (formats in the comments), for a site inside the fixed-point ranges.
-template <class O>
-__device__ __forceinline__ void collide_site_fx(const double (&f)[kQ], const StepParams& p, const FxSite& fs,
-                                                const O& out) {
+template <class O, class F>
+__device__ __forceinline__ void collide_site_fx(const F& f, const StepParams& p, const FxSite& fs, const O& out) {
   const long long UX = fs.UX, UY = fs.UY;  // Q64
   const long long TH = fs.TH;              // Q62
   const u64 R = fs.R;                      // Q61
@@ -446,7 +452,7 @@ __device__ __forceinline__ void collide_site_fx(const double (&f)[kQ], const Ste
   const u64 uK0 = (u64)K0, uK1 = (u64)K1 ^ kSign, uL0 = (u64)L0 ^ kSign;  // x + 2^63
   const u64 uM0 = (u64)M0 ^ kSign, uTH = (u64)rth ^ kSign;                // L1 = M1 = rth
   const double keep = p.one_minus_omega;
-  out.put(0, fma(keep, f[0], fx_to_double((long long)(__umul64hi(uK0, p.fx_c60[0]) - p.fx_d0[0]), p.fx_e[0], 0)));  // x2 = 0
+  out.put(0, fma(keep, f(0), fx_to_double((long long)(__umul64hi(uK0, p.fx_c60[0]) - p.fx_d0[0]), p.fx_e[0], 0)));  // x2 = 0
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
     const long long R0 = (long long)(__umul64hi(uK0, p.fx_c60[k]) + __umul64hi(uK1, p.fx_cx2_59[k]) +
@@ -469,8 +475,8 @@ __device__ __forceinline__ void collide_site_fx(const double (&f)[kQ], const Ste
       const long long s = R1 + (long long)umulhi_t(b, R3);              // Q57
       const long long oa = mulhi_su_rn(s, A);                            // Q55: |a| (R1 + b R3)
       const long long odd = (oa ^ sa) - sa;                              // the sign of a
-      out.put(1 + 2 * pr, fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E, k)));
-      out.put(2 + 2 * pr, fma(keep, f[2 + 2 * pr], fx_to_double(even - odd, E, k)));
+      out.put(1 + 2 * pr, fma(keep, f(1 + 2 * pr), fx_to_double(even + odd, E, k)));
+      out.put(2 + 2 * pr, fma(keep, f(2 + 2 * pr), fx_to_double(even - odd, E, k)));
     }
   }
 }
@@ -479,8 +485,8 @@ __device__ __forceinline__ void collide_site_fx(const double (&f)[kQ], const Ste
 // u_bar = u + tau g, T_bar = T - tau^2 g^2 / D (Eq. MASTERSHIFT3, Eq. discrete).
 // The equilibrium is evaluated per pair as even +- odd parts with per-shell
 // coefficients (see ShellConsts), pre-scaled by omega rho w_shell.
-template <class O>
-__device__ __forceinline__ void collide_site_fp64(const double (&f)[kQ], const StepParams& p, double rho, double ux,
+template <class O, class F>
+__device__ __forceinline__ void collide_site_fp64(const F& f, const StepParams& p, double rho, double ux,
                                                   double uy, double T, const O& out) {
   const double ubx = ux;
   const double uby = uy + p.uy_shift;
@@ -497,7 +503,7 @@ __device__ __forceinline__ void collide_site_fp64(const double (&f)[kQ], const S
   const double keep = p.one_minus_omega;
   {
     const double C0 = A0 + th * (c_shell.alpha[0] + q * c_shell.beta[0] + th * c_shell.gamma[0]);
-    out.put(0, fma(keep, f[0], wr * c_shell.w[0] * C0));
+    out.put(0, fma(keep, f(0), wr * c_shell.w[0] * C0));
   }
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
@@ -514,22 +520,23 @@ __device__ __forceinline__ void collide_site_fp64(const double (&f)[kQ], const S
       const double b = a * a;
       const double even = P0 + b * (P2 + b * P4);
       const double odd = a * (P1 + b * P3);
-      out.put(1 + 2 * pr, fma(keep, f[1 + 2 * pr], even + odd));
-      out.put(2 + 2 * pr, fma(keep, f[2 + 2 * pr], even - odd));
+      out.put(1 + 2 * pr, fma(keep, f(1 + 2 * pr), even + odd));
+      out.put(2 + 2 * pr, fma(keep, f(2 + 2 * pr), even - odd));
     }
   }
 }
 
 // One site's collision: moments as exact integer sums, then the fixed-point
 // form inside its ranges, else the FP64 form; the relaxed populations to out.
-template <class O>
-__device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParams& p, const O& out) {
+// fr: where the relaxation reads the populations (f itself by default).
+template <class O, class F>
+__device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParams& p, const O& out, const F& fr) {
   long long r, jx, jy, e;
   int emax;
   FxSite fs;
   const bool sums = site_sums(f, r, jx, jy, e, emax);
   if (sums && fx_site_from_sums(r, jx, jy, e, emax, p, fs)) {
-    collide_site_fx(f, p, fs, out);
+    collide_site_fx(fr, p, fs, out);
     return;
   }
   double rho, ux, uy, T;
@@ -537,7 +544,12 @@ __device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParam
     moments_from_sums(r, jx, jy, e, emax, rho, ux, uy, T);
   else
     site_moments_fp64(f, rho, ux, uy, T);
-  collide_site_fp64(f, p, rho, ux, uy, T, out);
+  collide_site_fp64(fr, p, rho, ux, uy, T, out);
+}
+
+template <class O>
+__device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParams& p, const O& out) {
+  collide_site_to(f, p, out, PopRegs{f});
 }
 
 // Wall bc for a site of a wall band, applied to its gathered populations:
@@ -546,20 +558,40 @@ __device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParam
 // Missing ones become rho_w f^eq_l(1, 0, T_wall), rho_w = outgoing mass of the
 // column / sum of f^eq over the missing pairs, so the wall injects exactly the
 // mass that left through it (reading of Sec. "The propagate and bc Kernels").
+//
+// The outgoing mass is summed row by row, each row's populations in index
+// order, and the three row sums as (row 0 + row 1) + row 2: the same grouping
+// whether one thread sums the column (wall_density) or the three threads of a
+// column's wall rows each sum their own row and combine the sums by warp
+// shuffles (wall_band_kernel), so both give the same bits.
+__device__ __forceinline__ double wall_row_outgoing(const double* __restrict__ src, const StepParams& p, int x,
+                                                    int wall, int r) {
+  const int y = wall ? p.Ly - 1 - r : r;
+  const long long i = site_index(p, x, y);
+  double s = 0.0;
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) {
+    const int cy = vel_cy(l);
+    if (wall ? (cy > r) : (cy < -r)) s += src[l * p.plane + i];
+  }
+  return s;
+}
+
 __device__ __forceinline__ double wall_density(const double* __restrict__ src, const StepParams& p, int x,
                                                int wall) {
-  double out = 0.0;
+  const double s0 = wall_row_outgoing(src, p, x, wall, 0);
+  const double s1 = wall_row_outgoing(src, p, x, wall, 1);
+  const double s2 = wall_row_outgoing(src, p, x, wall, 2);
+  return ((s0 + s1) + s2) * p.inv_denom[wall];
+}
+
+// The missing populations of a wall-band site at row r from the wall.
+__device__ __forceinline__ void apply_wall(double (&f)[kQ], const StepParams& p, int wall, int r, double rho_w) {
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    const int y = wall ? p.Ly - 1 - r : r;
-    const long long i = site_index(p, x, y);
-#pragma unroll
-    for (int l = 0; l < kQ; ++l) {
-      const int cy = vel_cy(l);
-      if (wall ? (cy > r) : (cy < -r)) out += src[l * p.plane + i];
-    }
+  for (int l = 0; l < kQ; ++l) {
+    const int cy = vel_cy(l);
+    if (wall ? (cy < -r) : (cy > r)) f[l] = rho_w * p.fw[wall][l];
   }
-  return out * p.inv_denom[wall];
 }
 
 // Write the populations of physical site (x, y) and, for sites within 3 of a
@@ -693,13 +725,7 @@ __device__ __forceinline__ void fused_site(const double* __restrict__ src, doubl
   }
   if (WALLS && !p.periodic_y && (y < 3 || y >= p.Ly - 3)) {
     const int wall = y >= p.Ly - 3;
-    const int r = wall ? p.Ly - 1 - y : y;
-    const double rho_w = wall_density(src, p, x, wall);
-#pragma unroll
-    for (int l = 0; l < kQ; ++l) {
-      const int cy = vel_cy(l);
-      if (wall ? (cy < -r) : (cy > r)) f[l] = rho_w * p.fw[wall][l];
-    }
+    apply_wall(f, p, wall, wall ? p.Ly - 1 - y : y, wall_density(src, p, x, wall));
   }
   // each pair straight to the site's planes, then the halo images, if any
   if constexpr (OFF)
@@ -723,9 +749,13 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(c
 }
 
 // The fused step of the six wall-band rows of every column (y = 0..2 and
-// Ly - 3..Ly - 1, walls only): packed 32 sites to a warp, so that the wall
-// bc's work runs in full warps instead of in three lanes of a fused_kernel
-// warp (a warp holding wall rows cost about three ordinary warps there).
+// Ly - 3..Ly - 1, walls only), packed into full warps so that the wall bc's
+// work runs at warp width instead of in three lanes of a fused_kernel warp (a
+// warp holding wall rows cost about three ordinary warps there).  Each warp
+// takes ten (column, wall) groups of three lanes, one lane per wall row (lanes
+// 30 and 31 idle); every lane sums the populations of its own row that leave
+// through the wall, and the group's three row sums meet by warp shuffles, so
+// the column's outgoing mass is read once instead of once per wall site.
 // When it is launched as a programmatic dependent of fused_kernel it may run
 // while that kernel's last blocks still run; every thread then waits for the
 // sites kernel to complete (griddepcontrol.wait: the prerequisite grid has
@@ -734,12 +764,30 @@ __global__ void __launch_bounds__(kBlockY, D2Q37_SITE_MIN_BLOCKS) fused_kernel(c
 // (the next step's sites kernel reads both kernels' rows) is ordered after
 // both, in a stream and in a captured graph alike.  Launched normally, the
 // wait returns at once.
+constexpr int kWallGroupsPerWarp = 10;
+
 __global__ void __launch_bounds__(kWallBlock) wall_band_kernel(const double* __restrict__ src,
                                                               double* __restrict__ dst, StepParams p) {
-  const int t = blockIdx.x * kWallBlock + threadIdx.x;
-  if (t < 6 * p.Lx) {
-    const int x = t / 6, k = t - 6 * x;
-    fused_site<true, true>(src, dst, p, p, x, k < 3 ? k : p.Ly - 6 + k);
+  const int lane = threadIdx.x & 31;
+  const int g = (blockIdx.x * (kWallBlock / 32) + (threadIdx.x >> 5)) * kWallGroupsPerWarp + lane / 3;
+  const int r = lane - 3 * (lane / 3);  // row from the wall
+  const bool active = lane < 3 * kWallGroupsPerWarp && g < 2 * p.Lx;
+  const int x = g >> 1, wall = g & 1;
+  const double s = active ? wall_row_outgoing(src, p, x, wall, r) : 0.0;
+  const int base = lane - r;  // the group's row-0 lane (idle lanes read lanes 30, 31, 32 mod 32)
+  const double s0 = __shfl_sync(0xffffffffu, s, base);
+  const double s1 = __shfl_sync(0xffffffffu, s, base + 1);
+  const double s2 = __shfl_sync(0xffffffffu, s, base + 2);
+  if (active) {
+    const int y = wall ? p.Ly - 1 - r : r;
+    const long long i = site_index(p, x, y);
+    double f[kQ];
+    const char* sp = (const char*)(src + i);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(sp + p.pull_off[l]);
+    apply_wall(f, p, wall, r, ((s0 + s1) + s2) * p.inv_denom[wall]);
+    collide_site_to(f, p, ToPlanes{(char*)(dst + i), p});
+    store_images<true>(dst, p, x, y);
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
@@ -817,6 +865,12 @@ __global__ void __launch_bounds__(kBlockY) init_equilibrium32_kernel(float* __re
 
 dim3 site_grid(const StepParams& p) { return dim3(p.Lx, (p.Ly + kBlockY - 1) / kBlockY); }
 
+// (column, wall) groups of the wall-band kernel: 2 Lx, ten per warp
+int wall_grid(const StepParams& p) {
+  constexpr int per_block = kWallGroupsPerWarp * (kWallBlock / 32);
+  return (2 * p.Lx + per_block - 1) / per_block;
+}
+
 int done(int n) { return cudaGetLastError() == cudaSuccess ? n : -1; }
 
 }  // namespace
@@ -851,11 +905,11 @@ int launch_fused(const double* src, double* dst, const StepParams& p, cudaStream
   fused_kernel<<<site_grid(p), kBlockY, 0, stream>>>(src, dst, p);
   if (p.periodic_y) return done(1);
   if (!overlap) {
-    wall_band_kernel<<<(6 * p.Lx + kWallBlock - 1) / kWallBlock, kWallBlock, 0, stream>>>(src, dst, p);
+    wall_band_kernel<<<wall_grid(p), kWallBlock, 0, stream>>>(src, dst, p);
     return done(2);
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((6 * p.Lx + kWallBlock - 1) / kWallBlock);
+  cfg.gridDim = dim3(wall_grid(p));
   cfg.blockDim = dim3(kWallBlock);
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
