@@ -75,8 +75,8 @@ def parse():
     ap.add_argument("--serving-budget-gb", type=float, default=96.0)
     ap.add_argument("--serving-steps-per-tick", type=int, default=16)
     ap.add_argument("--serving-time-limit", type=float, default=90.0)
-    ap.add_argument("--accuracy-steps", type=int, default=100,
-                    help="steps after which the FP32-storage forms are compared with the FP64 step")
+    ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
+                    help="skip the comparison with the oracle's stored fields")
     ap.add_argument("--Lx", type=int, default=2048)
     ap.add_argument("--Ly", type=int, default=8192)
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -410,6 +410,55 @@ def run_serving(a, dev):
             "budget_gb": a.serving_budget_gb, "max_steps_per_tick": a.serving_steps_per_tick, "runs": runs}
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "rt_2048x8192_seed1.npz")
+
+
+def oracle_errors(rho, u, T, z, n):
+    """Errors of one state against the oracle's stored fields after n steps:
+    per field max |a - b| / max |b| (u over both components) on the stored
+    sites and on the row and column means, and the relative L2 error over the
+    stored sites."""
+    sx, sy = z["sample_x"], z["sample_y"]
+    mx = z["n%d_max_abs" % n]
+    vals = {"rho": rho, "ux": u[0], "uy": u[1], "T": T}
+    scale = {"rho": mx[0], "ux": mx[1], "uy": mx[1], "T": mx[2]}
+    err, l2n, l2d = {}, {}, {}
+    for k, v in vals.items():
+        ref = z["n%d_%s_sample" % (n, k)]
+        got = v[sx, sy]
+        err[k] = max(np.abs(got - ref).max(), np.abs(v.mean(axis=0) - z["n%d_%s_rowmean" % (n, k)]).max(),
+                     np.abs(v.mean(axis=1) - z["n%d_%s_colmean" % (n, k)]).max()) / scale[k]
+        l2n[k], l2d[k] = ((got - ref) ** 2).sum(), (ref ** 2).sum()
+    return {"max_rel": {"rho": float(err["rho"]), "u": float(max(err["ux"], err["uy"])), "T": float(err["T"])},
+            "rel_l2_sample": {"rho": float(np.sqrt(l2n["rho"] / l2d["rho"])),
+                              "u": float(np.sqrt((l2n["ux"] + l2n["uy"]) / (l2d["ux"] + l2d["uy"]))),
+                              "T": float(np.sqrt(l2n["T"] / l2d["T"]))}}
+
+
+def accuracy_vs_oracle(torch, lbm, a, dev):
+    """Every precision form of the 2048 x 8192 workload (seed 1) stepped to the
+    step counts of the oracle's stored fields (tests/golden, written by a
+    script that runs only the oracle) and compared with them."""
+    if (a.Lx, a.Ly) != (2048, 8192) or not os.path.exists(GOLDEN):
+        return {}
+    z = np.load(GOLDEN)
+    counts = sorted(int(n) for n in z["steps"])
+    out = {}
+    for prec in ("fp64", "fp32", "fp32-df"):
+        lat = lbm.Lattice(a.Lx, a.Ly, tau=0.8, g0=1e-4, T_top=0.5, T_bot=1.5, kernel="fused", precision=prec,
+                          device=dev, stream=torch.cuda.Stream(device=dev))
+        lat.init_rayleigh_taylor(1)
+        done, res = 0, {}
+        for n in counts:
+            lat.step(n - done)
+            done = n
+            res["after_%d_steps" % n] = oracle_errors(*lat.fields(), z, n)
+        lat.close()
+        out[prec] = dict(res, oracle="FP64 CPU oracle, 2048x8192 seed 1: 8192 uniform sites, 3 full columns, "
+                                     "3 full rows, all row and column means")
+    return out
+
+
 def run_ours(a):
     rank, local_rank, world = dist_env()
     cpu = None
@@ -460,33 +509,22 @@ def run_ours(a):
                "steps": a.e2e_steps}
     lat.close()
 
-    # the FP32-storage forms on the same workload, each against the FP64 step's fields
+    # errors against the FP64 CPU oracle's stored fields of this workload (seed 1)
+    accuracy = accuracy_vs_oracle(torch, lbm, a, dev) if (rank == 0 and world == 1 and a.accuracy) else {}
+    # the FP32-storage forms on the same workload
     forms = {}
     if a.precision_forms and a.precision == "fp64":
-        ref = lbm.Lattice(a.Lx, a.Ly, device=dev)
-        ref.init_rayleigh_taylor(1 + rank)
-        ref.step(a.accuracy_steps)
-        ref_fields = ref.fields()
-        ref.close()
         for prec in ("fp32", "fp32-df"):
             flat, fms, fl, fkt, _ = time_form(torch, lbm, a, dev, prec, "fused", a.steps, 1 + rank)
             flat.close()
             fkind = max(fkt, key=lambda k: fkt[k][0])
-            acc = lbm.Lattice(a.Lx, a.Ly, device=dev, precision=prec)
-            acc.init_rayleigh_taylor(1 + rank)
-            acc.step(a.accuracy_steps)
-            fields = acc.fields()
-            acc.close()
-            errs = [float(np.linalg.norm(x - y) / np.linalg.norm(y)) for x, y in zip(fields, ref_fields)]
             forms[prec] = {"value": round(sites * a.steps / (fms * 1e-3) / 1e6, 3), "unit": UNIT,
                            "ms_per_step": round(fms / a.steps, 4), "dtype": DTYPES[prec],
                            "roofline": roofline_of(fkind, fkt[fkind][0] / a.steps * 1e-3, sites, prec,
                                                    FUSED32_DF_TRAFFIC_BYTES_2048x8192
                                                    if (fkind == "fused" and prec == "fp32-df" and
                                                        (a.Lx, a.Ly) == (2048, 8192)) else None),
-                           "rel_l2_vs_fp64_after_%d_steps" % a.accuracy_steps:
-                               {"rho": errs[0], "u": errs[1], "T": errs[2]},
-                           "gpu_launches": fl}
+                           "vs_oracle": accuracy.get(prec), "gpu_launches": fl}
     separate = separate_form(torch, lbm, a, dev) if (a.precision_forms and a.precision == "fp64" and
                                                      a.kernel == "fused") else None
     batched = run_batched(torch, lbm, a, dev) if (a.batched and a.precision == "fp64") else None
@@ -502,6 +540,7 @@ def run_ours(a):
                                  (37 * (a.Lx + 6) * (a.Ly + 32) * (8 if a.precision == "fp64" else 4) / 1e9),
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "vs_oracle": accuracy.get(a.precision),
                 "kernel_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1]}, "clocks": clocks,
                 "precision_forms": forms or None, "separate_form": separate, "batched_forms": batched, "serving": serving_summary}
         print(json.dumps(line), flush=True)
