@@ -365,20 +365,32 @@ def run_batched(torch, lbm, a, dev):
             lats.append(lat)
         b = lbm.Batch(lats)
         tune = b.autotune(trial_steps=3, use_cache=False)
-        b.step(a.warmup)
-        b.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n0 = b.launch_count
-        e0.record(b.stream)
-        b.step(a.batched_steps)
-        e1.record(b.stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        out[prec] = {"value": round(sites * a.batched_steps / (ms * 1e-3) / 1e6, 3), "unit": UNIT,
-                     "ms_per_step": round(ms / a.batched_steps, 4), "steps": a.batched_steps,
-                     "gpu_launches": b.launch_count - n0, "launch_shape": tune,
-                     "hbm_frac": round(BYTES_PER_SITE[prec] * sites * a.batched_steps / (ms * 1e-3) / 1e9 /
-                                       measured_peaks().get("hbm_gbs", float("nan")), 4)}
+
+        def timed():
+            b.step(a.warmup)
+            b.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n0 = b.launch_count
+            e0.record(b.stream)
+            b.step(a.batched_steps)
+            e1.record(b.stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            return {"value": round(sites * a.batched_steps / (ms * 1e-3) / 1e6, 3), "unit": UNIT,
+                    "ms_per_step": round(ms / a.batched_steps, 4), "steps": a.batched_steps,
+                    "gpu_launches": b.launch_count - n0,
+                    "hbm_frac": round(BYTES_PER_SITE[prec] * sites * a.batched_steps / (ms * 1e-3) / 1e9 /
+                                      measured_peaks().get("hbm_gbs", float("nan")), 4)}
+
+        out[prec] = dict(timed(), launch_shape=tune)
+        # every shape beside the autotuner's pick: one launch per step (block_y
+        # rows per tile, one block per tile), and one launch per lattice
+        shapes = {}
+        for by, bps in ((64, 0), (128, 0), (256, 0), (0, 0)):
+            b.set_config(by, bps)
+            shapes["block_y=%d" % by if by else "per_lattice"] = timed()
+        b.set_config(tune["block_y"], tune["blocks_per_sm"])
+        out[prec]["shapes"] = shapes
         b.close()
         for lat in lats:
             lat.close()

@@ -28,6 +28,11 @@ struct lbm_batch_t {
   int* dev_tile_entry[3];  // owning entry of every tile
   bool uniform;            // every lattice has the collision constants of `common` (same tau, g)
   StepParams common;
+  // FP64 with walls, shared tau and g, at most kBatchGeoMax lattices whose
+  // offsets fit 32 bits: block_y > 0 with blocks_per_sm = 0 runs the split
+  // form (site tiles and wall tiles in one launch), parameters per block_y
+  bool split_ok;
+  BatchLaunch* split[3];
   long long tiles[3];
   int block_y;        // 64, 128 or 256
   int blocks_per_sm;  // 0: one block per tile; else a persistent grid of blocks_per_sm x SMs
@@ -112,6 +117,12 @@ long long grid_of(const lbm_batch_t* b, int block_y, int blocks_per_sm) {
 int launch(lbm_batch_t* b, int block_y, int blocks_per_sm, int parity) {
   if (block_y == 0) return launch_each(b, parity);
   const int s = slot_of(block_y);
+  if (blocks_per_sm == 0 && b->split_ok) {
+    const int n = launch_batch_split(*b->split[s], b->dev_tab[s], b->dev_tile_entry[s], parity, block_y, b->stream);
+    if (n < 0) return LBM_ECUDA;
+    b->launches += n;
+    return LBM_OK;
+  }
   const int grid = (int)grid_of(b, block_y, blocks_per_sm);
   const int n = b->prec == LBM_PRECISION_FP64
                     ? launch_batch_fused(b->dev_tab[s], b->dev_tile_entry[s], b->n, b->tiles[s], parity, block_y,
@@ -160,6 +171,60 @@ bool pair_graph(lbm_batch_t* b, cudaGraphExec_t* out) {
   }
   *out = b->graph2;
   return true;
+}
+
+bool fits32(long long v) { return v >= -2147483647LL - 1 && v <= 2147483647LL; }
+
+// The split form's launch parameters for every block_y, if the batch allows it.
+void build_split(lbm_batch_t* b) {
+  b->split_ok = b->prec == LBM_PRECISION_FP64 && b->uniform && b->n <= kBatchGeoMax;
+  for (int i = 0; i < b->n && b->split_ok; ++i) {
+    const StepParams& q = b->lat[i]->sp;
+    b->split_ok = !q.periodic_y;
+    for (int l = 0; l < kQ && b->split_ok; ++l) b->split_ok = fits32(q.pull_off[l]) && fits32(q.plane_off[l]);
+  }
+  if (!b->split_ok) return;
+  const int bys[3] = {64, 128, 256};
+  for (int s = 0; s < 3; ++s) {
+    BatchLaunch* L = new BatchLaunch();
+    std::memset(L, 0, sizeof(*L));
+    L->common = b->common;
+    L->n = b->n;
+    long long t0 = 0, w0 = 0;
+    const int per_wall_tile = batch_wall_groups_per_tile(bys[s]);
+    for (int i = 0; i < b->n; ++i) {
+      const lbm_t* h = b->lat[i];
+      BatchGeo& g = L->g[i];
+      for (int l = 0; l < kQ; ++l) {
+        g.pull_off[l] = (int)h->sp.pull_off[l];
+        g.plane_off[l] = (int)h->sp.plane_off[l];
+      }
+      g.Lx = h->Lx;
+      g.Ly = h->Ly;
+      g.NY = h->sp.NY;
+      g.Hy = h->sp.Hy;
+      g.ytiles = (h->Ly + bys[s] - 1) / bys[s];
+      g.tile0 = (int)t0;
+      g.wtile0 = (int)w0;
+      g.cur = b->host_tab[s][i].cur;
+      g.entry = i;
+      g.plane = h->sp.plane;
+      g.buf[0] = h->buf[0];
+      g.buf[1] = h->buf[1];
+      g.inv_denom[0] = h->sp.inv_denom[0];
+      g.inv_denom[1] = h->sp.inv_denom[1];
+      t0 += (long long)h->Lx * g.ytiles;
+      w0 += (2LL * h->Lx + per_wall_tile - 1) / per_wall_tile;
+    }
+    if (t0 + w0 > 2147483647LL) {
+      delete L;
+      b->split_ok = false;
+      return;
+    }
+    L->site_tiles = (int)t0;
+    L->wall_tiles = (int)w0;
+    b->split[s] = L;
+  }
 }
 
 }  // namespace
@@ -240,6 +305,7 @@ int lbm_batch_create(int n, lbm_t* const* lattices, void* cuda_stream, lbm_batch
     if (!rc) rc = check(cudaStreamSynchronize(b->stream));
   }
   if (!rc) rc = check(cudaStreamSynchronize(b->stream));
+  if (!rc) build_split(b);
   if (rc) {
     lbm_batch_destroy(b);
     return rc;
@@ -370,6 +436,7 @@ void lbm_batch_destroy(lbm_batch_t* b) {
     if (t) cudaFree(t);
   for (int* t : b->dev_tile_entry)
     if (t) cudaFree(t);
+  for (BatchLaunch* L : b->split) delete L;
   delete b;
 }
 

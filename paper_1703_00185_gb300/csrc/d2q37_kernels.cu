@@ -51,7 +51,9 @@ constexpr int kWallBlock = 128;
 #define D2Q37_BATCH_MIN_BLOCKS 4
 #endif
 
-__device__ __forceinline__ long long site_index(const StepParams& p, int x, int y) {
+// P: StepParams or BatchGeo (NY, Hy)
+template <class P>
+__device__ __forceinline__ long long site_index(const P& p, int x, int y) {
   return (long long)(x + kHx) * p.NY + (y + p.Hy);
 }
 
@@ -564,8 +566,9 @@ __device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParam
 // whether one thread sums the column (wall_density) or the three threads of a
 // column's wall rows each sum their own row and combine the sums by warp
 // shuffles (wall_band_kernel), so both give the same bits.
-__device__ __forceinline__ double wall_row_outgoing(const double* __restrict__ src, const StepParams& p, int x,
-                                                    int wall, int r) {
+template <class P>  // StepParams or BatchGeo (Ly, NY, Hy, plane)
+__device__ __forceinline__ double wall_row_outgoing(const double* __restrict__ src, const P& p, int x, int wall,
+                                                    int r) {
   const int y = wall ? p.Ly - 1 - r : r;
   const long long i = site_index(p, x, y);
   double s = 0.0;
@@ -585,12 +588,13 @@ __device__ __forceinline__ double wall_density(const double* __restrict__ src, c
   return ((s0 + s1) + s2) * p.inv_denom[wall];
 }
 
-// The missing populations of a wall-band site at row r from the wall.
-__device__ __forceinline__ void apply_wall(double (&f)[kQ], const StepParams& p, int wall, int r, double rho_w) {
+// The missing populations of a wall-band site at row r from the wall; fw:
+// the wall's equilibrium f^eq_l(1, 0, T_wall).
+__device__ __forceinline__ void apply_wall(double (&f)[kQ], const double* fw, int wall, int r, double rho_w) {
 #pragma unroll
   for (int l = 0; l < kQ; ++l) {
     const int cy = vel_cy(l);
-    if (wall ? (cy < -r) : (cy > r)) f[l] = rho_w * p.fw[wall][l];
+    if (wall ? (cy < -r) : (cy > r)) f[l] = rho_w * fw[l];
   }
 }
 
@@ -725,7 +729,7 @@ __device__ __forceinline__ void fused_site(const double* __restrict__ src, doubl
   }
   if (WALLS && !p.periodic_y && (y < 3 || y >= p.Ly - 3)) {
     const int wall = y >= p.Ly - 3;
-    apply_wall(f, p, wall, wall ? p.Ly - 1 - y : y, wall_density(src, p, x, wall));
+    apply_wall(f, p.fw[wall], wall, wall ? p.Ly - 1 - y : y, wall_density(src, p, x, wall));
   }
   // each pair straight to the site's planes, then the halo images, if any
   if constexpr (OFF)
@@ -785,7 +789,7 @@ __global__ void __launch_bounds__(kWallBlock) wall_band_kernel(const double* __r
     const char* sp = (const char*)(src + i);
 #pragma unroll
     for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(sp + p.pull_off[l]);
-    apply_wall(f, p, wall, r, ((s0 + s1) + s2) * p.inv_denom[wall]);
+    apply_wall(f, p.fw[wall], wall, r, ((s0 + s1) + s2) * p.inv_denom[wall]);
     collide_site_to(f, p, ToPlanes{(char*)(dst + i), p});
     store_images<true>(dst, p, x, y);
   }
@@ -814,6 +818,111 @@ __global__ void __launch_bounds__(BY, (D2Q37_BATCH_MIN_BLOCKS * 128) / BY > 0 ? 
     if (y < e.p.Ly)
       fused_site<false>((const double*)e.buf[c], (double*)e.buf[c ^ 1], e.p, UNIFORM ? common : e.p, x, y);
   }
+}
+
+// ---- many lattices in one launch, split into site tiles and wall tiles ----
+//
+// One block per tile, no grid-stride loop: the blocks of site tiles (one
+// column x BY rows, the wall rows left out) run fused_kernel's per-site work,
+// and the blocks of wall tiles run wall_band_kernel's (three lanes per
+// column and wall, the outgoing mass combined by warp shuffles), so that no
+// warp of the launch holds a few wall rows among ordinary ones.  Every
+// lattice's offsets come from the launch's parameter space (BatchLaunch,
+// through the constant cache) and its collision constants from `common`; the
+// per-site arithmetic is the single-lattice kernels', so results are the same
+// bit for bit.  Requires walls, the same tau and g for every lattice and
+// offsets that fit 32 bits (checked on the host).
+static_assert(sizeof(BatchLaunch) <= 32764, "BatchLaunch must fit the kernel parameter space");
+
+struct GeoPlanes {
+  char* d;  // the site's element of plane 0
+  const BatchGeo& g;
+  __device__ __forceinline__ void put(int l, double v) const { *(double*)(d + g.plane_off[l]) = v; }
+};
+
+// The lattice owning block b of the site tiles (wall = false) or wall tiles.
+__device__ __forceinline__ int split_owner(const BatchLaunch& L, int b, bool wall) {
+  int lo = 0, hi = L.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((wall ? L.g[mid].wtile0 : L.g[mid].tile0) <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// The x halo image(s) of a site of a walled lattice (copied from dst[i]).
+__device__ __forceinline__ void split_images(double* __restrict__ dst, const BatchGeo& g, int x, long long i) {
+  if (x >= kHx && x < g.Lx - kHx) return;
+  const char* s = (const char*)(dst + i);
+  double f[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(s + g.plane_off[l]);
+  const long long shift = (long long)g.Lx * g.NY;
+  if (x < kHx) {
+    char* d = (char*)(dst + i + shift);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) *(double*)(d + g.plane_off[l]) = f[l];
+  }
+  if (x >= g.Lx - kHx) {
+    char* d = (char*)(dst + i - shift);
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) *(double*)(d + g.plane_off[l]) = f[l];
+  }
+}
+
+template <int BY>
+__global__ void __launch_bounds__(BY, (D2Q37_BATCH_MIN_BLOCKS * 128) / BY > 0 ? (D2Q37_BATCH_MIN_BLOCKS * 128) / BY : 1)
+    batch_split_kernel(const __grid_constant__ BatchLaunch L, const BatchEntry* __restrict__ tab,
+                       const int* __restrict__ tile_entry, int parity) {
+  const int b = blockIdx.x;
+  if (b < L.site_tiles) {
+    const BatchGeo& g = L.g[tile_entry[b]];
+    // x fastest, as in fused_kernel: the columns a tile pulls from run at the same time
+    const int local = b - g.tile0;
+    const int yt = local / g.Lx;
+    const int x = local - yt * g.Lx;
+    const int y = yt * BY + threadIdx.x;
+    if (y < 3 || y >= g.Ly - 3) return;  // the wall tiles'
+    const int c = g.cur ^ parity;
+    const long long i = site_index(g, x, y);
+    const char* s = (const char*)((const double*)g.buf[c] + i);
+    double f[kQ];
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(s + g.pull_off[l]);
+    double* dst = (double*)g.buf[c ^ 1];
+    collide_site_to(f, L.common, GeoPlanes{(char*)(dst + i), g});
+    split_images(dst, g, x, i);
+    return;
+  }
+  // wall tile: kWallGroupsPerWarp (column, wall) groups per warp, one lane per wall row
+  const int w = b - L.site_tiles;
+  const BatchGeo& g = L.g[split_owner(L, w, true)];
+  const int lane = threadIdx.x & 31;
+  const int grp = ((w - g.wtile0) * (BY / 32) + (threadIdx.x >> 5)) * kWallGroupsPerWarp + lane / 3;
+  const int r = lane - 3 * (lane / 3);
+  const bool active = lane < 3 * kWallGroupsPerWarp && grp < 2 * g.Lx;
+  const int x = grp >> 1, wall = grp & 1;
+  const int c = g.cur ^ parity;
+  const double* src = (const double*)g.buf[c];
+  const double sum = active ? wall_row_outgoing(src, g, x, wall, r) : 0.0;
+  const int base = lane - r;
+  const double s0 = __shfl_sync(0xffffffffu, sum, base);
+  const double s1 = __shfl_sync(0xffffffffu, sum, base + 1);
+  const double s2 = __shfl_sync(0xffffffffu, sum, base + 2);
+  if (!active) return;
+  const int y = wall ? g.Ly - 1 - r : r;
+  const long long i = site_index(g, x, y);
+  const char* s = (const char*)(src + i);
+  double f[kQ];
+#pragma unroll
+  for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(s + g.pull_off[l]);
+  apply_wall(f, tab[g.entry].p.fw[wall], wall, r, ((s0 + s1) + s2) * g.inv_denom[wall]);
+  double* dst = (double*)g.buf[c ^ 1];
+  collide_site_to(f, L.common, GeoPlanes{(char*)(dst + i), g});
+  split_images(dst, g, x, i);
 }
 
 __global__ void __launch_bounds__(kBlockY) fields_kernel(const double* __restrict__ buf, double* __restrict__ rho,
@@ -947,6 +1056,20 @@ int launch_batch_fused(const BatchEntry* tab, const int* tile_entry, int n, long
     default: return -1;
   }
 }
+
+int launch_batch_split(const BatchLaunch& L, const BatchEntry* tab, const int* tile_entry, int parity, int block_y,
+                       cudaStream_t stream) {
+  const int grid = L.site_tiles + L.wall_tiles;
+  switch (block_y) {
+    case 64: batch_split_kernel<64><<<grid, 64, 0, stream>>>(L, tab, tile_entry, parity); break;
+    case 128: batch_split_kernel<128><<<grid, 128, 0, stream>>>(L, tab, tile_entry, parity); break;
+    case 256: batch_split_kernel<256><<<grid, 256, 0, stream>>>(L, tab, tile_entry, parity); break;
+    default: return -1;
+  }
+  return done(1);
+}
+
+int batch_wall_groups_per_tile(int block_y) { return (block_y / 32) * kWallGroupsPerWarp; }
 
 int batch_blocks_per_sm(int block_y) {
   switch (block_y) {

@@ -169,6 +169,35 @@ struct BatchEntry {
   long long tile0;  // first tile of this lattice
 };
 
+// One lattice of a split batched launch (FP64, walls): its geometry, with
+// the 37 pull and plane offsets as 32-bit byte offsets, in the launch's
+// parameter space (BatchLaunch), where every block reads it through the
+// constant cache.  Site tiles are one column x `block_y` rows (the rows
+// outside the wall bands); wall tiles hold kBatchWallGroups (column, wall)
+// groups of three wall rows each.
+struct BatchGeo {
+  int pull_off[kQ];   // byte offset from a site to the source of its pull
+  int plane_off[kQ];  // byte offset from a site to its element of plane l
+  int Lx, Ly, NY, Hy;
+  int ytiles;         // site tiles per column
+  int tile0, wtile0;  // first site tile and first wall tile of this lattice
+  int cur;            // buffer holding the state when the launch parity is 0
+  int entry;          // index of this lattice in the BatchEntry table (wall equilibria)
+  long long plane;    // population plane stride (elements)
+  void* buf[2];
+  double inv_denom[2];
+};
+
+constexpr int kBatchGeoMax = 64;       // lattices per split launch (parameter space: 32 KB)
+constexpr int kBatchWallGroups = 40;   // (column, wall) groups per wall tile: 10 per warp, 4 warps
+
+struct BatchLaunch {
+  StepParams common;  // the collision constants every lattice shares (same tau and g)
+  int n;
+  int site_tiles, wall_tiles;
+  BatchGeo g[kBatchGeoMax];
+};
+
 // Index of the entry owning tile t (entries sorted by tile0, tile0[0] = 0).
 __device__ __forceinline__ int batch_entry_of(const BatchEntry* __restrict__ tab, int n, long long t) {
   int lo = 0, hi = n - 1;

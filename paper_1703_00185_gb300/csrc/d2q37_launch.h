@@ -42,6 +42,12 @@ int launch_init_equilibrium32(float* buf, const double* T, const StepParams& p, 
 int launch_batch_fused(const BatchEntry* tab, const int* tile_entry, int n, long long tiles, int parity,
                        int block_y, int grid, const StepParams* common, cudaStream_t stream);
 int batch_blocks_per_sm(int block_y);
+// The split form of the batched FP64 step (one launch: site tiles, then wall
+// tiles; see BatchLaunch); the (column, wall) groups one wall tile holds.
+// tile_entry: owning lattice of every site tile (the batch's per-tile table).
+int launch_batch_split(const BatchLaunch& L, const BatchEntry* tab, const int* tile_entry, int parity, int block_y,
+                       cudaStream_t stream);
+int batch_wall_groups_per_tile(int block_y);
 int launch_batch_fused32(const BatchEntry* tab, const int* tile_entry, int n, long long tiles, int parity,
                          int block_y, int grid, bool wide_fp64, cudaStream_t stream);
 int batch32_blocks_per_sm(int block_y, bool wide_fp64);
