@@ -256,14 +256,17 @@ int lbm_batch_step_static(int n, lbm_t* const* lattices, int steps, void* cuda_s
  * submission and are admitted, in arrival order with later jobs allowed to
  * pass ones that do not fit yet, whenever their device memory
  * (lbm_required_bytes) fits in the free part of one pre-allocated pool of
- * hbm_budget_bytes.  Each lbm_server_tick admits what fits, advances every
- * admitted job by k = min(max_steps_per_tick, fewest steps left) steps of
- * its fused step (as lbm_step: replays of a captured two-step graph) on the
- * job's stream (one of four, assigned at admission to the one with the fewest
- * active sites, so that the jobs run side by side), then copies the fields of
- * jobs that reached their step count to host memory and frees their device
- * memory.
- * All calls are from one host thread; a tick synchronises its streams. */
+ * hbm_budget_bytes.  Each lbm_server_tick first completes the jobs whose
+ * fields have arrived (copies them to host memory, frees their device memory),
+ * admits what fits, then advances every admitted job by
+ * min(max_steps_per_tick, its steps left) steps of its fused step (as
+ * lbm_step: replays of captured graphs) on the job's stream (one of eight,
+ * assigned at admission to the one with the fewest active sites, so that the
+ * jobs run side by side); a job that reaches its step count gets its fields
+ * computed on the device, to be completed by a later tick.
+ * All calls are from one host thread.  A tick waits for the GPU only to stay
+ * at most two ticks ahead of it, or, when every active job is waiting for its
+ * fields, for the first of them. */
 typedef struct lbm_server_t lbm_server_t;
 
 #define LBM_JOB_QUEUED 0
@@ -272,7 +275,7 @@ typedef struct lbm_server_t lbm_server_t;
 
 typedef struct {
   int64_t submitted, completed, queued, active;
-  int64_t ticks, steps, launches; /* ticks run, steps advanced, kernels launched */
+  int64_t ticks, steps, launches; /* ticks run, steps advanced (summed over jobs), kernels launched */
   size_t budget_bytes, bytes_in_use, largest_free_bytes;
 } lbm_server_stats;
 
@@ -286,8 +289,8 @@ int lbm_server_create(size_t hbm_budget_bytes, int max_steps_per_tick, lbm_serve
 int lbm_server_submit(lbm_server_t* s, int Lx, int Ly, int steps, const lbm_params* p, uint64_t seed,
                       int64_t* job_id);
 
-/* One scheduling round (see above); *steps_done (may be NULL) = k, 0 when no
- * job is active. */
+/* One scheduling round (see above); *steps_done (may be NULL) = the most
+ * steps any job advanced in it, 0 when none did. */
 int lbm_server_tick(lbm_server_t* s, int* steps_done);
 
 /* Ids of jobs completed since the last poll (at most max_ids); *n = count. */

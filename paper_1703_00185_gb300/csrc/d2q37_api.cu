@@ -360,13 +360,14 @@ int step_once(lbm_t* h, int phases, bool fused) {
   return rc;
 }
 
-// Two fused steps captured once per starting buffer and replayed: one graph
-// launch instead of two kernel launches.  Returns false (and the caller
-// launches directly) when the stream cannot be captured, e.g. the legacy
-// default stream.
-bool fused_pair_graph(lbm_t* h, cudaGraphExec_t* out) {
+// An even number of fused steps (2 or kLongGraphSteps) captured once per
+// starting buffer and replayed: one graph launch instead of one kernel launch
+// per kernel.  Returns false (and the caller launches directly) when the
+// stream cannot be captured, e.g. the legacy default stream.
+bool fused_graph(lbm_t* h, int steps, cudaGraphExec_t* out) {
   if (h->graph_unavailable) return false;
-  cudaGraphExec_t& g = h->graph2[h->cur];
+  const bool lng = steps == kLongGraphSteps;
+  cudaGraphExec_t& g = lng ? h->graph_long[h->cur] : h->graph2[h->cur];
   if (!g) {
     const int c = h->cur;
     cudaGraph_t graph = nullptr;
@@ -375,10 +376,16 @@ bool fused_pair_graph(lbm_t* h, cudaGraphExec_t* out) {
       h->graph_unavailable = true;
       return false;
     }
-    const int n1 = k_fused(h, h->buf[c], h->buf[1 - c]);
-    const int n2 = k_fused(h, h->buf[1 - c], h->buf[c]);
+    int launched = 0;
+    bool ok = true;
+    for (int k = 0; k < steps; ++k) {
+      const int from = (k & 1) ? 1 - c : c;
+      const int nk = k_fused(h, h->buf[from], h->buf[1 - from]);
+      ok = ok && nk >= 0;
+      launched += nk;
+    }
     const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
-    if (e != cudaSuccess || n1 < 0 || n2 < 0 || cudaGraphInstantiate(&g, graph, 0) != cudaSuccess) {
+    if (e != cudaSuccess || !ok || cudaGraphInstantiate(&g, graph, 0) != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();
       g = nullptr;
@@ -386,7 +393,7 @@ bool fused_pair_graph(lbm_t* h, cudaGraphExec_t* out) {
       return false;
     }
     cudaGraphDestroy(graph);
-    h->graph2_launches = n1 + n2;
+    (lng ? h->graph_long_launches : h->graph2_launches) = launched;
   }
   *out = g;
   return true;
@@ -589,10 +596,15 @@ int lbm_step(lbm_t* h, int n) {
       ++t;
     }
     cudaGraphExec_t g;
-    while (n - t >= 2 && fused_pair_graph(h, &g)) {
+    while (n - t >= kLongGraphSteps && fused_graph(h, kLongGraphSteps, &g)) {
+      if (cudaGraphLaunch(g, h->stream) != cudaSuccess) return LBM_ECUDA;
+      h->launches += h->graph_long_launches;
+      t += kLongGraphSteps;  // an even number of swaps: the current buffer is unchanged
+    }
+    while (n - t >= 2 && fused_graph(h, 2, &g)) {
       if (cudaGraphLaunch(g, h->stream) != cudaSuccess) return LBM_ECUDA;
       h->launches += h->graph2_launches;
-      t += 2;  // two swaps: the current buffer is unchanged
+      t += 2;
     }
   }
   for (; t < n; ++t) {
@@ -668,6 +680,8 @@ void lbm_destroy(lbm_t* h) {
   drain_timing(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   for (cudaGraphExec_t g : h->graph2)
+    if (g) cudaGraphExecDestroy(g);
+  for (cudaGraphExec_t g : h->graph_long)
     if (g) cudaGraphExecDestroy(g);
   if (h->owns_stream && h->stream) cudaStreamDestroy(h->stream);
   if (h->owned) cudaFree(h->owned);

@@ -29,6 +29,8 @@ struct lbm_t {
   int64_t launches;
   cudaGraphExec_t graph2[2];  // two fused steps starting from buffer 0 / 1
   int64_t graph2_launches;  // kernels in one replay of graph2 (2 steps)
+  cudaGraphExec_t graph_long[2];  // kLongGraphSteps fused steps from buffer 0 / 1
+  int64_t graph_long_launches;
   bool graph_unavailable;
   // per-kernel timing: event pairs recorded around launches, folded into the
   // totals when the stream is synchronised
@@ -44,6 +46,9 @@ struct lbm_t {
 };
 
 namespace d2q37 {
+
+// Fused steps per replay of a handle's long graph (lbm_step with n >= this).
+constexpr int kLongGraphSteps = 16;
 
 // Launch the pbc kernel on `stream` if the handle's halos are stale.
 int handle_prepare_halos(lbm_t* h, cudaStream_t stream);

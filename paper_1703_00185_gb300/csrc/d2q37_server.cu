@@ -6,13 +6,16 @@
 // that fits, whenever their device memory fits in the free part of one
 // pre-allocated pool (the HBM budget; first-fit with coalescing).  Admitted
 // jobs keep their state on the device.  Each tick advances every active job
-// by k steps, k = min(steps per tick, fewest steps left), through its own
-// handle's step (replays of captured two-step graphs of the fused step) on
-// the job's stream: one of kStreams streams, assigned at admission to the one
-// with the fewest active sites, so that the jobs run side by side (on GB300
-// per-job launches beat one batched launch per step over all jobs by 14-30 %).  A job that reaches its step count has its
-// fields copied to host memory and its device memory returned to the pool;
-// the next tick can admit queued jobs into it.
+// by min(steps per tick, its steps left) steps through its own handle's step
+// (replays of captured 16- and 2-step graphs of the fused step) on the job's
+// stream: one of kStreams streams, assigned at admission to the one with the
+// fewest active sites, so that the jobs run side by side (on GB300 per-job
+// launches beat one batched launch per step over all jobs by 14-30 %).  A job
+// that reaches its step count has its fields computed into its scratch and
+// an event recorded behind them; a later tick, once the event has passed,
+// copies them to host memory and returns the job's device memory to the pool,
+// so that queued jobs can be admitted into it.  Ticks do not wait for the GPU
+// except to stay at most two ticks ahead of it.
 #include <algorithm>
 #include <cstring>
 #include <deque>
@@ -26,7 +29,8 @@
 
 namespace {
 
-constexpr int kStreams = 4;
+constexpr int kStreams = 8;
+constexpr int kTicksAhead = 2;  // ticks the host may enqueue ahead of the GPU
 
 struct Job {
   int64_t id;
@@ -37,6 +41,8 @@ struct Job {
   size_t bytes, offset;
   lbm_t* h;
   int stream;  // index into lbm_server_t::stream
+  bool draining;        // fields enqueued into the scratch, waiting for done_ev
+  cudaEvent_t done_ev;  // recorded behind the fields kernel
   std::vector<double> rho, u, T;  // results once done
 };
 
@@ -100,12 +106,18 @@ struct lbm_server_t {
   std::vector<int64_t> finished;  // not yet reported by lbm_server_poll
   cudaStream_t stream[kStreams];
   long long stream_sites[kStreams];  // sites of the active jobs on each stream
+  cudaEvent_t tick_ev[kTicksAhead][kStreams];  // the end of each stream's work of recent ticks
+  bool tick_ev_used[kTicksAhead];
   lbm_server_stats stats;
 };
 
 namespace {
 
 void release_job_memory(lbm_server_t* s, Job* j) {
+  if (j->done_ev) {
+    cudaEventDestroy(j->done_ev);
+    j->done_ev = nullptr;
+  }
   if (j->h) {
     lbm_destroy(j->h);
     j->h = nullptr;
@@ -148,6 +160,44 @@ int admit(lbm_server_t* s) {
   return LBM_OK;
 }
 
+// Jobs whose fields are ready: copy them to host memory, return the device
+// memory.  block: wait for the first draining job if none is ready.
+int finalize(lbm_server_t* s, bool block) {
+  bool any = false;
+  for (int pass = 0; pass < 2 && !any; ++pass) {
+    for (Job* j : s->active) {
+      if (!j->draining) continue;
+      cudaError_t e = cudaEventQuery(j->done_ev);
+      if (e == cudaErrorNotReady && pass == 1 && block) e = cudaEventSynchronize(j->done_ev);
+      if (e == cudaErrorNotReady) continue;
+      if (e != cudaSuccess) return LBM_ECUDA;
+      const size_t n = (size_t)j->Lx * j->Ly;
+      j->rho.resize(n);
+      j->u.resize(2 * n);
+      j->T.resize(n);
+      const double* sc = j->h->scratch;  // rho, ux, uy, T planes
+      if (cudaMemcpy(j->rho.data(), sc, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+          cudaMemcpy(j->u.data(), sc + n, 2 * n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+          cudaMemcpy(j->T.data(), sc + 3 * n, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return LBM_ECUDA;
+      s->stream_sites[j->stream] -= (long long)j->Lx * j->Ly;
+      release_job_memory(s, j);
+      j->state = LBM_JOB_DONE;
+      j->draining = false;
+      s->finished.push_back(j->id);
+      s->stats.completed++;
+      any = true;
+      if (pass == 1) break;  // one blocking wait per call
+    }
+    if (!block) break;
+  }
+  if (any)
+    s->active.erase(std::remove_if(s->active.begin(), s->active.end(),
+                                   [](Job* j) { return j->state == LBM_JOB_DONE; }),
+                    s->active.end());
+  return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -168,8 +218,11 @@ int lbm_server_create(size_t hbm_budget_bytes, int max_steps_per_tick, lbm_serve
     return LBM_ENOMEM;
   }
   s->pool.reset(s->budget);
-  for (int g = 0; g < kStreams && !rc; ++g)
+  for (int g = 0; g < kStreams && !rc; ++g) {
     if (cudaStreamCreateWithFlags(&s->stream[g], cudaStreamNonBlocking) != cudaSuccess) rc = LBM_ECUDA;
+    for (int a = 0; a < kTicksAhead && !rc; ++a)
+      if (cudaEventCreateWithFlags(&s->tick_ev[a][g], cudaEventDisableTiming) != cudaSuccess) rc = LBM_ECUDA;
+  }
   if (rc) {
     lbm_server_destroy(s);
     return rc;
@@ -204,50 +257,51 @@ int lbm_server_submit(lbm_server_t* s, int Lx, int Ly, int steps, const lbm_para
 int lbm_server_tick(lbm_server_t* s, int* steps_done) {
   if (!s) return LBM_EINVAL;
   if (steps_done) *steps_done = 0;
-  int rc = admit(s);
+  int rc = finalize(s, false);
+  if (!rc) rc = admit(s);
   if (rc) return rc;
   if (s->active.empty()) return LBM_OK;
-  int k = s->max_steps_per_tick;
-  for (Job* j : s->active) k = std::min(k, j->steps_left);
-  // each job's k steps in order on its stream (lbm_step: replays of its
-  // captured two-step graphs, one host launch per two steps); the streams run
-  // side by side
+  // stay at most kTicksAhead ticks ahead of the GPU
+  const int slot = (int)(s->stats.ticks % kTicksAhead);
+  if (s->tick_ev_used[slot])
+    for (int g = 0; g < kStreams; ++g)
+      if (cudaEventSynchronize(s->tick_ev[slot][g]) != cudaSuccess) return LBM_ECUDA;
+  // each job's steps in order on its stream (lbm_step: replays of its captured
+  // graphs); the streams run side by side.  A job that reaches its step count
+  // gets its fields computed into its scratch, and an event behind them.
+  int kmax = 0;
   for (Job* j : s->active) {
-    const int64_t before = j->h->launches;
-    rc = lbm_step(j->h, k);
-    if (rc) return rc;
-    s->stats.launches += j->h->launches - before;
-  }
-  // completed jobs: fields into their scratch, then to host
-  std::vector<Job*> done;
-  for (Job* j : s->active) {
-    j->steps_left -= k;
-    if (j->steps_left == 0) done.push_back(j);
-  }
-  for (Job* j : done) {
-    const size_t n = (size_t)j->Lx * j->Ly;
-    j->rho.resize(n);
-    j->u.resize(2 * n);
-    j->T.resize(n);
-    rc = lbm_fields(j->h, j->rho.data(), j->u.data(), j->T.data());  // on the job's stream, synchronising
-    if (rc) return rc;
+    if (j->draining) continue;
+    const int k = std::min(s->max_steps_per_tick, j->steps_left);
+    if (k > 0) {
+      const int64_t before = j->h->launches;
+      rc = lbm_step(j->h, k);
+      if (rc) return rc;
+      s->stats.launches += j->h->launches - before;
+      j->steps_left -= k;
+      s->stats.steps += k;
+      kmax = std::max(kmax, k);
+    }
+    if (j->steps_left == 0) {
+      const size_t n = (size_t)j->Lx * j->Ly;
+      double* sc = j->h->scratch;
+      rc = lbm_fields_device(j->h, sc, sc + n, sc + 3 * n);
+      if (!rc && cudaEventCreateWithFlags(&j->done_ev, cudaEventDisableTiming) != cudaSuccess) rc = LBM_ECUDA;
+      if (!rc && cudaEventRecord(j->done_ev, s->stream[j->stream]) != cudaSuccess) rc = LBM_ECUDA;
+      if (rc) return rc;
+      j->draining = true;
+    }
   }
   for (int g = 0; g < kStreams; ++g)
-    if (cudaStreamSynchronize(s->stream[g]) != cudaSuccess) return LBM_ECUDA;
-  for (Job* j : done) {
-    s->stream_sites[j->stream] -= (long long)j->Lx * j->Ly;
-    release_job_memory(s, j);
-    j->state = LBM_JOB_DONE;
-    s->finished.push_back(j->id);
-    s->stats.completed++;
-  }
-  if (!done.empty())
-    s->active.erase(std::remove_if(s->active.begin(), s->active.end(),
-                                   [](Job* j) { return j->state == LBM_JOB_DONE; }),
-                    s->active.end());
+    if (cudaEventRecord(s->tick_ev[slot][g], s->stream[g]) != cudaSuccess) return LBM_ECUDA;
+  s->tick_ev_used[slot] = true;
   s->stats.ticks++;
-  s->stats.steps += k;
-  if (steps_done) *steps_done = k;
+  if (kmax == 0) {
+    // only jobs whose fields are on their way: wait for the first of them
+    rc = finalize(s, true);
+    if (rc) return rc;
+  }
+  if (steps_done) *steps_done = kmax;
   return LBM_OK;
 }
 
@@ -298,11 +352,15 @@ void lbm_server_destroy(lbm_server_t* s) {
   for (int g = 0; g < kStreams; ++g)
     if (s->stream[g]) cudaStreamSynchronize(s->stream[g]);
   for (auto& kv : s->jobs) {
+    if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
     if (kv.second->h) lbm_destroy(kv.second->h);
     delete kv.second;
   }
-  for (int g = 0; g < kStreams; ++g)
+  for (int g = 0; g < kStreams; ++g) {
     if (s->stream[g]) cudaStreamDestroy(s->stream[g]);
+    for (int a = 0; a < kTicksAhead; ++a)
+      if (s->tick_ev[a][g]) cudaEventDestroy(s->tick_ev[a][g]);
+  }
   if (s->pool_mem) cudaFree(s->pool_mem);
   delete s;
 }
