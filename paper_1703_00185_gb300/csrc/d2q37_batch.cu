@@ -12,6 +12,7 @@
 // lbm_batch_step(n) replays a captured two-step CUDA graph when the stream
 // can be captured (with block_y = 0 a graph of parallel branches).
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
@@ -33,6 +34,10 @@ struct lbm_batch_t {
   // form (site tiles and wall tiles in one launch), parameters per block_y
   bool split_ok;
   BatchLaunch* split[3];
+  // FP32 storage, at most kBatchGeo32Max lattices: block_y > 0 with
+  // blocks_per_sm = 0 runs one block per tile with parameters in the launch
+  bool split32_ok;
+  BatchLaunch32* split32[3];
   long long tiles[3];
   int block_y;        // 64, 128 or 256
   int blocks_per_sm;  // 0: one block per tile; else a persistent grid of blocks_per_sm x SMs
@@ -117,8 +122,11 @@ long long grid_of(const lbm_batch_t* b, int block_y, int blocks_per_sm) {
 int launch(lbm_batch_t* b, int block_y, int blocks_per_sm, int parity) {
   if (block_y == 0) return launch_each(b, parity);
   const int s = slot_of(block_y);
-  if (blocks_per_sm == 0 && b->split_ok) {
-    const int n = launch_batch_split(*b->split[s], b->dev_tab[s], b->dev_tile_entry[s], parity, block_y, b->stream);
+  if (blocks_per_sm == 0 && (b->split_ok || b->split32_ok)) {
+    const int n = b->split_ok ? launch_batch_split(*b->split[s], b->dev_tab[s], b->dev_tile_entry[s], parity,
+                                                   block_y, b->stream)
+                              : launch_batch_split32(*b->split32[s], b->dev_tile_entry[s], (int)b->tiles[s], parity,
+                                                     block_y, b->prec == LBM_PRECISION_FP32_FP64, b->stream);
     if (n < 0) return LBM_ECUDA;
     b->launches += n;
     return LBM_OK;
@@ -174,6 +182,50 @@ bool pair_graph(lbm_batch_t* b, cudaGraphExec_t* out) {
 }
 
 bool fits32(long long v) { return v >= -2147483647LL - 1 && v <= 2147483647LL; }
+
+// The FP32 one-block-per-tile form's launch parameters (the lattices'
+// entries of the device table dev_tab hold their wall constants).
+void build_split32(lbm_batch_t* b) {
+  b->split32_ok = b->prec != LBM_PRECISION_FP64 && b->n <= kBatchGeo32Max;
+  for (int s = 0; s < 3 && b->split32_ok; ++s) {
+    if (b->tiles[s] > 2147483647LL) {
+      b->split32_ok = false;
+      break;
+    }
+    BatchLaunch32* L = new BatchLaunch32();
+    std::memset(L, 0, sizeof(*L));
+    L->n = b->n;
+    for (int i = 0; i < b->n; ++i) {
+      const lbm_t* h = b->lat[i];
+      const StepParams& q = h->sp;
+      // device addresses inside the entry's parameters (addresses only: no access on the host)
+      const char* dq = (const char*)b->dev_tab[s] + i * sizeof(BatchEntry) + offsetof(BatchEntry, p);
+      BatchGeo32& g = L->g[i];
+      g.Lx = h->Lx;
+      g.Ly = h->Ly;
+      g.NY = q.NY;
+      g.Hy = q.Hy;
+      g.periodic_y = q.periodic_y;
+      g.tile0 = (int)b->host_tab[s][i].tile0;
+      g.cur = b->host_tab[s][i].cur;
+      g.plane = q.plane;
+      g.buf[0] = h->buf[0];
+      g.buf[1] = h->buf[1];
+      g.omega_f = q.omega_f;
+      g.keep_f = q.keep_f;
+      g.uy_shift_df[0] = q.uy_shift_df[0];
+      g.uy_shift_df[1] = q.uy_shift_df[1];
+      g.theta_shift_df[0] = q.theta_shift_df[0];
+      g.theta_shift_df[1] = q.theta_shift_df[1];
+      g.theta_shift = q.theta_shift;
+      g.fw32 = (const float(*)[kQ])(dq + offsetof(StepParams, fw32));
+      g.fwmw32 = (const float(*)[kQ])(dq + offsetof(StepParams, fwmw32));
+      g.wall_e32 = (const float(*)[2])(dq + offsetof(StepParams, wall_e32));
+      g.wall_inv32 = (const float(*)[2])(dq + offsetof(StepParams, wall_inv32));
+    }
+    b->split32[s] = L;
+  }
+}
 
 // The split form's launch parameters for every block_y, if the batch allows it.
 void build_split(lbm_batch_t* b) {
@@ -305,7 +357,10 @@ int lbm_batch_create(int n, lbm_t* const* lattices, void* cuda_stream, lbm_batch
     if (!rc) rc = check(cudaStreamSynchronize(b->stream));
   }
   if (!rc) rc = check(cudaStreamSynchronize(b->stream));
-  if (!rc) build_split(b);
+  if (!rc) {
+    build_split(b);
+    build_split32(b);
+  }
   if (rc) {
     lbm_batch_destroy(b);
     return rc;
@@ -437,6 +492,7 @@ void lbm_batch_destroy(lbm_batch_t* b) {
   for (int* t : b->dev_tile_entry)
     if (t) cudaFree(t);
   for (BatchLaunch* L : b->split) delete L;
+  for (BatchLaunch32* L : b->split32) delete L;
   delete b;
 }
 

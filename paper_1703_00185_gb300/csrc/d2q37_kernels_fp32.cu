@@ -32,7 +32,8 @@ constexpr int kBlockY = 128;
 #define D2Q37_FP32_MIN_BLOCKS 6
 #endif
 
-__device__ __forceinline__ long long site_index(const StepParams& p, int x, int y) {
+template <class P>  // StepParams or BatchGeo32 (NY, Hy)
+__device__ __forceinline__ long long site_index(const P& p, int x, int y) {
   return (long long)(x + kHx) * p.NY + (y + p.Hy);
 }
 
@@ -222,8 +223,9 @@ __device__ __forceinline__ float fixed_to_float(long long v, int ex) {
 // in their theta-parts, G0_k, rho, E, T).  The velocity (|u| << 1) enters
 // only through a = xi.u_bar and q = |u_bar|^2, whose FP32 errors are scaled
 // down by |u|, and the q-parts of K0, K1 are ~q theta: FP32.
-template <class W>
-__device__ __forceinline__ void collide_site32(float (&d)[kQ], const StepParams& p) {
+// P: StepParams, or BatchGeo32 (the same collision fields)
+template <class W, class P>
+__device__ __forceinline__ void collide_site32(float (&d)[kQ], const P& p) {
   using T = typename W::T;
   const ShellConsts32& c = c_shell32;
   const Sums sm = deviation_sums(d);
@@ -356,7 +358,8 @@ __device__ __forceinline__ void fields_of_site32(const float (&d)[kQ], double& r
 }
 
 // Halo images as in the FP64 store_site.
-__device__ __forceinline__ void store_site32(float* __restrict__ dst, const StepParams& p, int x, int y,
+template <class P>
+__device__ __forceinline__ void store_site32(float* __restrict__ dst, const P& p, int x, int y,
                                              const float (&d)[kQ]) {
   if (x >= kHx && x < p.Lx - kHx && (!p.periodic_y || (y >= kHx && y < p.Ly - kHx))) {
     float* q = dst + (int)site_index(p, x, y);  // no halo image: the common case
@@ -390,7 +393,8 @@ __device__ __forceinline__ void store_site32(float* __restrict__ dst, const Step
 //   rho_w - 1 = (sum_O d - E) / D,   E = B - sum_O w + sum_M w,
 // with E and 1/D carried as (hi, lo) float pairs, so that no rounding of a
 // constant biases the wall's mass the same way every step.
-__device__ __forceinline__ float wall_rho_minus_1(const float* __restrict__ src, const StepParams& p, int x,
+template <class P>
+__device__ __forceinline__ float wall_rho_minus_1(const float* __restrict__ src, const P& p, int x,
                                                   int wall) {
   float out_d = 0.0f;
 #pragma unroll
@@ -407,7 +411,8 @@ __device__ __forceinline__ float wall_rho_minus_1(const float* __restrict__ src,
   return fmaf(t, p.wall_inv32[wall][0], t * p.wall_inv32[wall][1]);
 }
 
-__device__ __forceinline__ float missing32(const StepParams& p, float rho_w_minus_1, int wall, int l) {
+template <class P>
+__device__ __forceinline__ float missing32(const P& p, float rho_w_minus_1, int wall, int l) {
   return fmaf(rho_w_minus_1, p.fw32[wall][l], p.fwmw32[wall][l]);
 }
 
@@ -442,9 +447,9 @@ __global__ void __launch_bounds__(256) wrap32_kernel(float* __restrict__ buf, St
 
 // One site of the fused step (pull, wall bc on the wall bands, collide,
 // store with halo images).
-template <class W>
-__device__ __forceinline__ void fused_site32(const float* __restrict__ src, float* __restrict__ dst,
-                                             const StepParams& p, int x, int y) {
+template <class W, class P>
+__device__ __forceinline__ void fused_site32(const float* __restrict__ src, float* __restrict__ dst, const P& p,
+                                             int x, int y) {
   // the site's pointer once per thread; each population at an offset that is
   // the same for the whole block (l plane - cx NY - cy)
   const float* q = src + (int)site_index(p, x, y);
@@ -487,6 +492,27 @@ __global__ void __launch_bounds__(BY, (D2Q37_FP32_MIN_BLOCKS * 128) / BY) batch_
     const int c = e.cur ^ parity;
     if (y < e.p.Ly) fused_site32<W>((const float*)e.buf[c], (float*)e.buf[c ^ 1], e.p, x, y);
   }
+}
+
+// Many lattices in one launch, one block per tile (a column x BY rows, x
+// fastest, as fused32_kernel orders its blocks), no grid-stride loop: each
+// lattice's geometry and collision constants come from the launch's parameter
+// space (BatchLaunch32), its wall constants from its entry of the table.  The
+// per-site arithmetic is fused32_kernel's.
+static_assert(sizeof(BatchLaunch32) <= 32764, "BatchLaunch32 must fit the kernel parameter space");
+
+template <class W, int BY>
+__global__ void __launch_bounds__(BY, (D2Q37_FP32_MIN_BLOCKS * 128) / BY)
+    batch_split32_kernel(const __grid_constant__ BatchLaunch32 L, const int* __restrict__ tile_entry, int parity) {
+  const int b = blockIdx.x;
+  const BatchGeo32& g = L.g[tile_entry[b]];
+  const int local = b - g.tile0;
+  const int yt = local / g.Lx;
+  const int x = local - yt * g.Lx;
+  const int y = yt * BY + threadIdx.x;
+  if (y >= g.Ly) return;
+  const int c = g.cur ^ parity;
+  fused_site32<W>((const float*)g.buf[c], (float*)g.buf[c ^ 1], g, x, y);
 }
 
 __global__ void __launch_bounds__(kBlockY) propagate32_kernel(const float* __restrict__ src, float* __restrict__ dst,
@@ -648,6 +674,25 @@ int launch_batch_fused32(const BatchEntry* tab, const int* tile_entry, int n, lo
                                : batch32_launch<WideDF, 128>(tab, tile_entry, n, tiles, parity, grid, stream);
     case 256: return wide_fp64 ? batch32_launch<WideF64, 256>(tab, tile_entry, n, tiles, parity, grid, stream)
                                : batch32_launch<WideDF, 256>(tab, tile_entry, n, tiles, parity, grid, stream);
+    default: return -1;
+  }
+}
+
+template <class W, int BY>
+int split32_launch(const BatchLaunch32& L, const int* tile_entry, int tiles, int parity, cudaStream_t stream) {
+  batch_split32_kernel<W, BY><<<tiles, BY, 0, stream>>>(L, tile_entry, parity);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_batch_split32(const BatchLaunch32& L, const int* tile_entry, int tiles, int parity, int block_y,
+                         bool wide_fp64, cudaStream_t stream) {
+  switch (block_y) {
+    case 64: return wide_fp64 ? split32_launch<WideF64, 64>(L, tile_entry, tiles, parity, stream)
+                              : split32_launch<WideDF, 64>(L, tile_entry, tiles, parity, stream);
+    case 128: return wide_fp64 ? split32_launch<WideF64, 128>(L, tile_entry, tiles, parity, stream)
+                               : split32_launch<WideDF, 128>(L, tile_entry, tiles, parity, stream);
+    case 256: return wide_fp64 ? split32_launch<WideF64, 256>(L, tile_entry, tiles, parity, stream)
+                               : split32_launch<WideDF, 256>(L, tile_entry, tiles, parity, stream);
     default: return -1;
   }
 }

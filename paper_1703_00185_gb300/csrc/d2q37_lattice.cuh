@@ -198,6 +198,31 @@ struct BatchLaunch {
   BatchGeo g[kBatchGeoMax];
 };
 
+// One lattice of a split batched launch in FP32 storage (BatchLaunch32): the
+// fields of StepParams that the FP32 per-site code reads, under the same
+// names, with the wall constants as pointers into the lattice's entry of the
+// BatchEntry table (device memory; only wall rows read them).
+struct BatchGeo32 {
+  int Lx, Ly, NY, Hy, periodic_y;
+  int tile0, cur;
+  long long plane;
+  void* buf[2];
+  float omega_f, keep_f;
+  float uy_shift_df[2], theta_shift_df[2];
+  double theta_shift;
+  const float (*fw32)[kQ];
+  const float (*fwmw32)[kQ];
+  const float (*wall_e32)[2];
+  const float (*wall_inv32)[2];
+};
+
+constexpr int kBatchGeo32Max = 128;  // lattices per split FP32 launch
+
+struct BatchLaunch32 {
+  int n;
+  BatchGeo32 g[kBatchGeo32Max];
+};
+
 // Index of the entry owning tile t (entries sorted by tile0, tile0[0] = 0).
 __device__ __forceinline__ int batch_entry_of(const BatchEntry* __restrict__ tab, int n, long long t) {
   int lo = 0, hi = n - 1;

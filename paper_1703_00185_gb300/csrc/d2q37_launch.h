@@ -51,6 +51,10 @@ int batch_wall_groups_per_tile(int block_y);
 int launch_batch_fused32(const BatchEntry* tab, const int* tile_entry, int n, long long tiles, int parity,
                          int block_y, int grid, bool wide_fp64, cudaStream_t stream);
 int batch32_blocks_per_sm(int block_y, bool wide_fp64);
+// FP32 storage, one block per tile with every lattice's parameters in the
+// launch's parameter space (BatchLaunch32); tiles: grid size.
+int launch_batch_split32(const BatchLaunch32& L, const int* tile_entry, int tiles, int parity, int block_y,
+                         bool wide_fp64, cudaStream_t stream);
 
 // One population plane between a contiguous FP64 [Lx][Ly] array (f) and the
 // FP32 deviation frame (d = f - w_l).
