@@ -834,10 +834,18 @@ __global__ void __launch_bounds__(BY, (D2Q37_BATCH_MIN_BLOCKS * 128) / BY > 0 ? 
 // offsets that fit 32 bits (checked on the host).
 static_assert(sizeof(BatchLaunch) <= 32764, "BatchLaunch must fit the kernel parameter space");
 
+
 struct GeoPlanes {
   char* d;  // the site's element of plane 0
   const BatchGeo& g;
   __device__ __forceinline__ void put(int l, double v) const { *(double*)(d + g.plane_off[l]) = v; }
+};
+
+// The same with the plane offsets from a shared-memory copy.
+struct SharedPlanes {
+  char* d;
+  const int* off;  // shared memory: plane offsets of the block's lattice
+  __device__ __forceinline__ void put(int l, double v) const { *(double*)(d + off[l]) = v; }
 };
 
 // The lattice owning block b of the site tiles (wall = false) or wall tiles.
@@ -880,6 +888,12 @@ __global__ void __launch_bounds__(BY, (D2Q37_BATCH_MIN_BLOCKS * 128) / BY > 0 ? 
   const int b = blockIdx.x;
   if (b < L.site_tiles) {
     const BatchGeo& g = L.g[tile_entry[b]];
+    // the lattice's 74 offsets in shared memory: the blocks of an SM serve
+    // different lattices, whose parameter slices crowd the constant cache
+    // (read from there: 5796 MLUPS on the 64-lattice workload, against 5881)
+    __shared__ int off[2 * kQ];
+    for (int k = threadIdx.x; k < 2 * kQ; k += BY) off[k] = k < kQ ? g.pull_off[k] : g.plane_off[k - kQ];  // BY may be < 74
+    __syncthreads();
     // x fastest, as in fused_kernel: the columns a tile pulls from run at the same time
     const int local = b - g.tile0;
     const int yt = local / g.Lx;
@@ -890,10 +904,10 @@ __global__ void __launch_bounds__(BY, (D2Q37_BATCH_MIN_BLOCKS * 128) / BY > 0 ? 
     const long long i = site_index(g, x, y);
     const char* s = (const char*)((const double*)g.buf[c] + i);
     double f[kQ];
-#pragma unroll
-    for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(s + g.pull_off[l]);
     double* dst = (double*)g.buf[c ^ 1];
-    collide_site_to(f, L.common, GeoPlanes{(char*)(dst + i), g});
+#pragma unroll
+    for (int l = 0; l < kQ; ++l) f[l] = *(const double*)(s + off[l]);
+    collide_site_to(f, L.common, SharedPlanes{(char*)(dst + i), off + kQ});
     split_images(dst, g, x, i);
     return;
   }
