@@ -505,7 +505,15 @@ template <class W, int BY>
 __global__ void __launch_bounds__(BY, (D2Q37_FP32_MIN_BLOCKS * 128) / BY)
     batch_split32_kernel(const __grid_constant__ BatchLaunch32 L, const int* __restrict__ tile_entry, int parity) {
   const int b = blockIdx.x;
-  const BatchGeo32& g = L.g[tile_entry[b]];
+  // the lattice's parameters in shared memory: the blocks of an SM serve
+  // different lattices, whose parameter slices would crowd the constant cache
+  __shared__ BatchGeo32 g;
+  static_assert(sizeof(BatchGeo32) % sizeof(int) == 0, "BatchGeo32 is copied as ints");
+  {
+    const int* from = (const int*)&L.g[tile_entry[b]];
+    for (int k = threadIdx.x; k < (int)(sizeof(BatchGeo32) / sizeof(int)); k += BY) ((int*)&g)[k] = from[k];
+  }
+  __syncthreads();
   const int local = b - g.tile0;
   const int yt = local / g.Lx;
   const int x = local - yt * g.Lx;
