@@ -348,8 +348,9 @@ def separate_form(torch, lbm, a, dev):
 
 
 def run_batched(torch, lbm, a, dev):
-    """a.batched_lattices (64) uneven Rayleigh-Taylor lattices advanced together, one launch per
-    step (graph-replayed), launch shape from the autotuner; FP64 and FP32."""
+    """a.batched_lattices (64) uneven Rayleigh-Taylor lattices advanced together (graph-replayed),
+    launch shape from the autotuner, and every shape beside it: one launch per step with
+    block_y rows per tile, or one launch per lattice; FP64 and FP32 storage."""
     from paper_1703_00185_gb300 import workloads
     jobs = workloads.batched_lattices(1, a.batched_lattices)
     sites = sum(j["Lx"] * j["Ly"] for j in jobs)
