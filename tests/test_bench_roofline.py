@@ -55,3 +55,30 @@ def test_without_measured_peaks(monkeypatch):
 def test_whole_job_rate():
     # sites x ranks x steps / seconds, in millions
     assert bench.whole_job_mlups(1000, 4, 10, 2.0) == pytest.approx(1000 * 4 * 10 / 2e-3 / 1e6)
+
+
+def test_oracle_errors_metric():
+    """bench.oracle_errors: per field max |a - b| / max |b| over the stored sites
+    and the row and column means (u over both components), and the relative L2
+    error over the stored sites, on a made-up state and stored summary."""
+    import numpy as np
+    rng = np.random.default_rng(5)
+    Lx, Ly, n = 6, 10, 7
+    ref = {"rho": rng.uniform(0.5, 2.0, (Lx, Ly)), "ux": rng.normal(0, 1e-2, (Lx, Ly)),
+           "uy": rng.normal(0, 1e-2, (Lx, Ly)), "T": rng.uniform(0.5, 1.5, (Lx, Ly))}
+    sx, sy = np.array([0, 5, 2, 3]), np.array([9, 0, 4, 4])
+    z = {"sample_x": sx, "sample_y": sy,
+         "n7_max_abs": np.array([np.abs(ref["rho"]).max(), max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max()),
+                                 np.abs(ref["T"]).max()])}
+    for k, v in ref.items():
+        z["n7_%s_sample" % k], z["n7_%s_rowmean" % k], z["n7_%s_colmean" % k] = v[sx, sy], v.mean(0), v.mean(1)
+    got = {k: v.copy() for k, v in ref.items()}
+    got["T"][2, 4] += 1e-9  # a stored site
+    got["uy"][1, 1] += 3e-9  # seen only through its row and column means
+    e = bench.oracle_errors(got["rho"], np.stack([got["ux"], got["uy"]]), got["T"], z, n)
+    assert e["max_rel"]["rho"] == 0.0
+    assert e["max_rel"]["T"] == pytest.approx(1e-9 / z["n7_max_abs"][2], rel=1e-6)
+    assert e["max_rel"]["u"] == pytest.approx(3e-9 / Lx / z["n7_max_abs"][1], rel=1e-6)  # the row mean
+    t = ref["T"][sx, sy]
+    assert e["rel_l2_sample"]["T"] == pytest.approx(1e-9 / np.sqrt((t ** 2).sum()), rel=1e-6)
+    assert e["rel_l2_sample"]["u"] == 0.0
