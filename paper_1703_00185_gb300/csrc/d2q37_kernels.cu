@@ -402,13 +402,6 @@ __device__ __forceinline__ bool fx_site_from_sums(long long r, long long jx, lon
   return true;
 }
 
-// Where the relaxation reads each population's pre-collision value (the
-// site's register array).
-struct PopRegs {
-  const double (&f)[kQ];
-  __device__ __forceinline__ double operator()(int l) const { return f[l]; }
-};
-
 // Where a collision puts the relaxed populations: straight into the site's
 // planes of the destination, so that each pair's registers are free once it
 // is relaxed.
@@ -425,8 +418,9 @@ struct ToPlanesStride {  // the same with the planes addressed as multiples of t
 
 // The collision of collide_site_fp64 below with the equilibrium in fixed
 // point (formats in the comments), for a site inside the fixed-point ranges.
-template <class O, class F>
-__device__ __forceinline__ void collide_site_fx(const F& f, const StepParams& p, const FxSite& fs, const O& out) {
+template <class O>
+__device__ __forceinline__ void collide_site_fx(const double (&f)[kQ], const StepParams& p, const FxSite& fs,
+                                                const O& out) {
   const long long UX = fs.UX, UY = fs.UY;  // Q64
   const long long TH = fs.TH;              // Q62
   const u64 R = fs.R;                      // Q61
@@ -454,7 +448,7 @@ __device__ __forceinline__ void collide_site_fx(const F& f, const StepParams& p,
   const u64 uK0 = (u64)K0, uK1 = (u64)K1 ^ kSign, uL0 = (u64)L0 ^ kSign;  // x + 2^63
   const u64 uM0 = (u64)M0 ^ kSign, uTH = (u64)rth ^ kSign;                // L1 = M1 = rth
   const double keep = p.one_minus_omega;
-  out.put(0, fma(keep, f(0), fx_to_double((long long)(__umul64hi(uK0, p.fx_c60[0]) - p.fx_d0[0]), p.fx_e[0], 0)));  // x2 = 0
+  out.put(0, fma(keep, f[0], fx_to_double((long long)(__umul64hi(uK0, p.fx_c60[0]) - p.fx_d0[0]), p.fx_e[0], 0)));  // x2 = 0
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
     const long long R0 = (long long)(__umul64hi(uK0, p.fx_c60[k]) + __umul64hi(uK1, p.fx_cx2_59[k]) +
@@ -477,8 +471,8 @@ __device__ __forceinline__ void collide_site_fx(const F& f, const StepParams& p,
       const long long s = R1 + (long long)umulhi_t(b, R3);              // Q57
       const long long oa = mulhi_su_rn(s, A);                            // Q55: |a| (R1 + b R3)
       const long long odd = (oa ^ sa) - sa;                              // the sign of a
-      out.put(1 + 2 * pr, fma(keep, f(1 + 2 * pr), fx_to_double(even + odd, E, k)));
-      out.put(2 + 2 * pr, fma(keep, f(2 + 2 * pr), fx_to_double(even - odd, E, k)));
+      out.put(1 + 2 * pr, fma(keep, f[1 + 2 * pr], fx_to_double(even + odd, E, k)));
+      out.put(2 + 2 * pr, fma(keep, f[2 + 2 * pr], fx_to_double(even - odd, E, k)));
     }
   }
 }
@@ -487,8 +481,8 @@ __device__ __forceinline__ void collide_site_fx(const F& f, const StepParams& p,
 // u_bar = u + tau g, T_bar = T - tau^2 g^2 / D (Eq. MASTERSHIFT3, Eq. discrete).
 // The equilibrium is evaluated per pair as even +- odd parts with per-shell
 // coefficients (see ShellConsts), pre-scaled by omega rho w_shell.
-template <class O, class F>
-__device__ __forceinline__ void collide_site_fp64(const F& f, const StepParams& p, double rho, double ux,
+template <class O>
+__device__ __forceinline__ void collide_site_fp64(const double (&f)[kQ], const StepParams& p, double rho, double ux,
                                                   double uy, double T, const O& out) {
   const double ubx = ux;
   const double uby = uy + p.uy_shift;
@@ -505,7 +499,7 @@ __device__ __forceinline__ void collide_site_fp64(const F& f, const StepParams& 
   const double keep = p.one_minus_omega;
   {
     const double C0 = A0 + th * (c_shell.alpha[0] + q * c_shell.beta[0] + th * c_shell.gamma[0]);
-    out.put(0, fma(keep, f(0), wr * c_shell.w[0] * C0));
+    out.put(0, fma(keep, f[0], wr * c_shell.w[0] * C0));
   }
 #pragma unroll
   for (int k = 1; k < kShells; ++k) {
@@ -522,23 +516,22 @@ __device__ __forceinline__ void collide_site_fp64(const F& f, const StepParams& 
       const double b = a * a;
       const double even = P0 + b * (P2 + b * P4);
       const double odd = a * (P1 + b * P3);
-      out.put(1 + 2 * pr, fma(keep, f(1 + 2 * pr), even + odd));
-      out.put(2 + 2 * pr, fma(keep, f(2 + 2 * pr), even - odd));
+      out.put(1 + 2 * pr, fma(keep, f[1 + 2 * pr], even + odd));
+      out.put(2 + 2 * pr, fma(keep, f[2 + 2 * pr], even - odd));
     }
   }
 }
 
 // One site's collision: moments as exact integer sums, then the fixed-point
 // form inside its ranges, else the FP64 form; the relaxed populations to out.
-// fr: where the relaxation reads the populations (f itself by default).
-template <class O, class F>
-__device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParams& p, const O& out, const F& fr) {
+template <class O>
+__device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParams& p, const O& out) {
   long long r, jx, jy, e;
   int emax;
   FxSite fs;
   const bool sums = site_sums(f, r, jx, jy, e, emax);
   if (sums && fx_site_from_sums(r, jx, jy, e, emax, p, fs)) {
-    collide_site_fx(fr, p, fs, out);
+    collide_site_fx(f, p, fs, out);
     return;
   }
   double rho, ux, uy, T;
@@ -546,12 +539,7 @@ __device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParam
     moments_from_sums(r, jx, jy, e, emax, rho, ux, uy, T);
   else
     site_moments_fp64(f, rho, ux, uy, T);
-  collide_site_fp64(fr, p, rho, ux, uy, T, out);
-}
-
-template <class O>
-__device__ __forceinline__ void collide_site_to(double (&f)[kQ], const StepParams& p, const O& out) {
-  collide_site_to(f, p, out, PopRegs{f});
+  collide_site_fp64(f, p, rho, ux, uy, T, out);
 }
 
 // Wall bc for a site of a wall band, applied to its gathered populations:
