@@ -176,13 +176,21 @@ void lbm_destroy(lbm_t* h);
 /* ---- batched stepping: many lattices, one launch per step -----------------
  * Not in the paper (its lattices are split across GPUs instead); this is the
  * single-GPU form for many independent jobs.  Every lattice keeps its own
- * memory, parameters and state (its lbm_t); the batch advances all of them by
- * one step per launch of a grid-stride fused kernel over tiles (one column by
- * block_y rows) of every lattice, or (block_y = 0) by one launch of the
- * single-lattice fused kernel per lattice, spread over four streams forked
- * from the batch stream and joined back to it; lbm_batch_step(n >= 4)
- * replays a captured two-step CUDA graph.  Per-site arithmetic is the fused
- * kernel's, so a lattice's result is the same batched or alone. */
+ * memory, parameters and state (its lbm_t).  Launch shapes:
+ *  - block_y > 0, blocks_per_sm = 0: one launch per step with one block per
+ *    tile (one column by block_y rows) of every lattice.  FP64 batches whose
+ *    lattices all have walls and the same tau and g (at most 64 lattices,
+ *    offsets within 32 bits) run the wall rows in separate wall tiles of the
+ *    same launch and read each lattice's offsets from the launch's parameters;
+ *    FP32-storage batches of at most 128 lattices read each lattice's
+ *    parameters from the launch's parameters; others use the table below.
+ *  - block_y > 0, blocks_per_sm > 0: a persistent grid-stride kernel over the
+ *    tiles, each lattice's parameters read from a device table.
+ *  - block_y = 0: one launch of the single-lattice fused kernel per lattice,
+ *    spread over four streams forked from the batch stream and joined back.
+ * lbm_batch_step(n >= 4) replays a captured two-step CUDA graph.  Per-site
+ * arithmetic is the fused kernel's, so a lattice's result is the same batched
+ * or alone. */
 typedef struct lbm_batch_t lbm_batch_t;
 
 /* Group n lattices (same precision, each with a state) on cuda_stream (NULL:
