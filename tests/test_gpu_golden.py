@@ -12,10 +12,10 @@ lattice-wide maxima and the totals.
 Metric (as everywhere in the FP64 tests): per field, max |a - b| / max |b|
 over the lattice (u over both components jointly), evaluated on the stored
 sites and on the row and column means.  Bars:
-  * FP64, 100 steps: 1e-12, the tolerance of the full FP64 step;
-  * FP64, 1000 steps: 1e-10, the aim stated for the 1000-step run (errors of
-    the unstable Rayleigh-Taylor flow grow with time; the measured values are
-    recorded beside the bench's numbers);
+  * FP64, 100 and 1000 steps: 1e-12, the tolerance of the full FP64 step
+    (measured after 1000 steps: rho 1.8e-13, u 2.3e-13, T 1.6e-13; the
+    unstable Rayleigh-Taylor flow amplifies rounding differences in time, and
+    the 1000-step run was only required to stay within 1e-10);
   * FP32 storage: relative L2 error over the stored sites, at the bars of the
     256 x 128 accuracy tests (measured errors times about 10).
 """
@@ -29,7 +29,7 @@ import paper_1703_00185_gb300 as lbm
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rt_2048x8192_seed1.npz")
-FP64_BARS = {100: 1e-12, 1000: 1e-10}
+FP64_BARS = {100: 1e-12, 1000: 1e-12}
 FP32_L2_BARS = {100: (2e-7, 5e-5, 2e-7), 1000: (1e-6, 1e-4, 1e-6)}
 
 
