@@ -68,7 +68,7 @@ def parse():
                     help="skip timing the FP32-storage forms after the FP64 step")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip timing the 64-lattice batched forms")
-    ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--batched-steps", type=int, default=500, help="steps of the batched workload (500)")
     ap.add_argument("--batched-lattices", type=int, default=64,
                     help="lattices in the batched form (64 is the workload; fewer make a small profiling case)")
     ap.add_argument("--serving-jobs", type=int, default=40, help="0 skips the serving run")
@@ -367,29 +367,30 @@ def run_batched(torch, lbm, a, dev):
         b = lbm.Batch(lats)
         tune = b.autotune(trial_steps=3, use_cache=False)
 
-        def timed():
+        def timed(steps):
             b.step(a.warmup)
             b.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             n0 = b.launch_count
             e0.record(b.stream)
-            b.step(a.batched_steps)
+            b.step(steps)
             e1.record(b.stream)
             e1.synchronize()
             ms = e0.elapsed_time(e1)
-            return {"value": round(sites * a.batched_steps / (ms * 1e-3) / 1e6, 3), "unit": UNIT,
-                    "ms_per_step": round(ms / a.batched_steps, 4), "steps": a.batched_steps,
+            return {"value": round(sites * steps / (ms * 1e-3) / 1e6, 3), "unit": UNIT,
+                    "ms_per_step": round(ms / steps, 4), "steps": steps,
                     "gpu_launches": b.launch_count - n0,
-                    "hbm_frac": round(BYTES_PER_SITE[prec] * sites * a.batched_steps / (ms * 1e-3) / 1e9 /
+                    "hbm_frac": round(BYTES_PER_SITE[prec] * sites * steps / (ms * 1e-3) / 1e9 /
                                       measured_peaks().get("hbm_gbs", float("nan")), 4)}
 
-        out[prec] = dict(timed(), launch_shape=tune)
-        # every shape beside the autotuner's pick: one launch per step (block_y
-        # rows per tile, one block per tile), and one launch per lattice
+        out[prec] = dict(timed(a.batched_steps), launch_shape=tune)
+        # every shape beside the autotuner's pick (100 steps each): one launch
+        # per step (block_y rows per tile, one block per tile), and one launch
+        # per lattice
         shapes = {}
         for by, bps in ((64, 0), (128, 0), (256, 0), (0, 0)):
             b.set_config(by, bps)
-            shapes["block_y=%d" % by if by else "per_lattice"] = timed()
+            shapes["block_y=%d" % by if by else "per_lattice"] = timed(min(100, a.batched_steps))
         b.set_config(tune["block_y"], tune["blocks_per_sm"])
         out[prec]["shapes"] = shapes
         b.close()
