@@ -3,12 +3,18 @@
 //
 // The lattices keep their own memory and parameters (lbm_t handles); the
 // batch owns a device table of BatchEntry (parameters, both buffers, the
-// buffer holding the state, tile range) and advances every lattice by one
-// step per launch of the batched fused kernel, walking the tiles of all
-// lattices with a grid-stride loop.  Launch shape block_y = 0 instead issues
-// the single-lattice fused kernel once per lattice (its parameters in the
-// constant bank), spread over kAux streams forked from and joined to the
-// batch stream, so that small lattices run side by side.
+// buffer holding the state, tile range) and a per-tile owner table, and
+// advances every lattice by one step per launch:
+//  - block_y > 0, blocks_per_sm = 0: one block per tile.  FP64 batches that
+//    allow it (walls, one tau and g, at most kBatchGeoMax lattices, 32-bit
+//    offsets) run the split form, site tiles and wall tiles of every lattice
+//    with each lattice's offsets in the launch's parameters (BatchLaunch);
+//    FP32-storage batches of at most kBatchGeo32Max lattices take their
+//    parameters from BatchLaunch32; other batches run the table kernel.
+//  - block_y > 0, blocks_per_sm > 0: the table kernel on a persistent grid.
+//  - block_y = 0: the single-lattice fused kernel once per lattice (its
+//    parameters in the constant bank), spread over kAux streams forked from
+//    and joined to the batch stream, so that small lattices run side by side.
 // lbm_batch_step(n) replays a captured two-step CUDA graph when the stream
 // can be captured (with block_y = 0 a graph of parallel branches).
 #include <algorithm>
