@@ -360,10 +360,12 @@ def _autotune_cache_path():
 
 
 class Batch:
-    """Many lattices advanced together, one launch of the batched fused kernel
-    per step (``lbm_batch_*``).  All lattices must share the precision and
-    have a state; while a batch is in use, step them only through it and call
-    :meth:`synchronize` before reading their fields."""
+    """Many lattices advanced together (``lbm_batch_*``): one launch per step
+    over the tiles of every lattice, or one launch per lattice on parallel
+    streams, as :meth:`set_config` or :meth:`autotune` choose.  All lattices
+    must share the precision and have a state; while a batch is in use, step
+    them only through it and call :meth:`synchronize` before reading their
+    fields."""
 
     def __init__(self, lattices, stream=None):
         import torch
