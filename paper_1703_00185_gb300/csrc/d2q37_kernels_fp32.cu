@@ -364,7 +364,10 @@ __device__ __forceinline__ void store_site32(float* __restrict__ dst, const P& p
   if (x >= kHx && x < p.Lx - kHx && (!p.periodic_y || (y >= kHx && y < p.Ly - kHx))) {
     float* q = dst + (int)site_index(p, x, y);  // no halo image: the common case
 #pragma unroll
-    for (int l = 0; l < kQ; ++l) q[l * p.plane] = d[l];
+    // streaming stores (evict-first): the next step reads these rows from
+    // DRAM anyway; 0.8378 -> 0.8293 ms per 2048 x 8192 step (streaming loads
+    // instead: 0.8931, the pull's rows are shared by neighbouring warps)
+    for (int l = 0; l < kQ; ++l) __stcs(q + l * p.plane, d[l]);
     return;
   }
   int xs[3] = {x, 0, 0}, ys[3] = {y, 0, 0};
