@@ -507,6 +507,7 @@ int lbm_create_ext(int Lx, int Ly, const lbm_params* p, void* dev_buf, size_t by
 }
 
 int lbm_init_rayleigh_taylor(lbm_t* h, uint64_t seed) {
+  const TraceRange trace("lbm_init_rayleigh_taylor");
   if (!h) return LBM_EINVAL;
   const int Lx = h->Lx, Ly = h->Ly;
   std::vector<double> T((size_t)Lx * Ly);
@@ -585,6 +586,7 @@ int lbm_get_populations(lbm_t* h, double* f) {
 }
 
 int lbm_step(lbm_t* h, int n) {
+  const TraceRange trace("lbm_step");
   if (!h || n < 0) return LBM_EINVAL;
   if (!h->have_state) return LBM_ESTATE;
   const bool fused = h->prm.kernel != LBM_KERNEL_SEPARATE;

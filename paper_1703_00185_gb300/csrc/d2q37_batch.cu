@@ -403,6 +403,7 @@ int lbm_batch_get_config(const lbm_batch_t* b, int* block_y, int* blocks_per_sm)
 }
 
 int lbm_batch_step(lbm_batch_t* b, int n) {
+  const TraceRange trace("lbm_batch_step");
   if (!b || n < 0) return LBM_EINVAL;
   int t = 0;
   if (n >= 4) {
@@ -429,6 +430,7 @@ int lbm_batch_step(lbm_batch_t* b, int n) {
 }
 
 int lbm_batch_autotune(lbm_batch_t* b, int trial_steps, int* block_y, int* blocks_per_sm, double* best_ms) {
+  const TraceRange trace("lbm_batch_autotune");
   if (!b || trial_steps <= 0) return LBM_EINVAL;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return LBM_ECUDA;

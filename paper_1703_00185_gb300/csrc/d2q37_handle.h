@@ -6,6 +6,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/d2q37.h"
 #include "d2q37_launch.h"
@@ -46,6 +47,15 @@ struct lbm_t {
 };
 
 namespace d2q37 {
+
+// An NVTX range over a scope (host side), so that profilers' timelines show
+// the library's entry points; free when no tool is attached.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Fused steps per replay of a handle's long graph (lbm_step with n >= this).
 constexpr int kLongGraphSteps = 16;

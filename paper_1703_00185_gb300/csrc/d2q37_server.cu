@@ -255,6 +255,7 @@ int lbm_server_submit(lbm_server_t* s, int Lx, int Ly, int steps, const lbm_para
 }
 
 int lbm_server_tick(lbm_server_t* s, int* steps_done) {
+  const TraceRange trace("lbm_server_tick");
   if (!s) return LBM_EINVAL;
   if (steps_done) *steps_done = 0;
   int rc = finalize(s, false);
